@@ -1,0 +1,233 @@
+/*
+ * gbqr.h -- C ABI of the graph-based density-matrix and response library.
+ *
+ * The library evaluates, on one GPU, the data-parallel hot path of graph-based
+ * canonical quantum perturbation theory at finite electronic temperature
+ * (Negre, Wall & Niklasson, arXiv:2212.01997):
+ *
+ *   gb_graph_build           thresholded data-dependency graph      (Sec. "Estimating the connectivity graph")
+ *   gb_partition             disjoint cores + distance-1 halos       (Fig. 1; Sec. "Choosing the graph partitioning")
+ *   gb_density_and_response  D, D1, mu, mu1 on the partitioned graph (Eqs. Fermi, DD0-DD, NewtonRaphson,
+ *                                                                      D1, ddlambda, dddmu, dmu_1, dCollect)
+ *
+ * Conventions for every entry point:
+ *   - Plain C types only.  Pointers marked [device] are CUDA device pointers,
+ *     [host] are host pointers.  All memory is owned by the caller; the library
+ *     allocates no device memory.  Scratch comes from the caller's workspace
+ *     (gb_set_workspace).
+ *   - Work is enqueued on the handle's stream.  Calls that must return sizes or
+ *     scalars to the host (partition sizes, mu, traces) synchronise that stream.
+ *   - Every function returns a gb_status (0 = GB_OK).  None throws, aborts or
+ *     traps; device-side waits are bounded and report GB_ERR_TIMEOUT.
+ *   - Energies (H, H1, kT, mu) are in eV.  Matrices are square n x n.
+ *   - Orthogonal basis (the paper's orthogonalised representation).
+ */
+#ifndef GBQR_H
+#define GBQR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gb_status {
+    GB_OK = 0,
+    GB_ERR_ARG = 1,          /* invalid argument (null pointer, bad size, kT <= 0, ...)      */
+    GB_ERR_CAPACITY = 2,     /* an output array is too small; the needed size is reported   */
+    GB_ERR_WORKSPACE = 3,    /* workspace too small; see gb_required_workspace              */
+    GB_ERR_MU_BRACKET = 4,   /* N_occ cannot be reached for any mu (Ne out of range)        */
+    GB_ERR_NO_CONVERGE = 5,  /* mu iteration hit max_newton without meeting the tolerance   */
+    GB_ERR_NAN = 6,          /* a non-finite value appeared in the input or the result      */
+    GB_ERR_DEVICE = 7,       /* a CUDA runtime call failed                                  */
+    GB_ERR_UNSUPPORTED = 8,  /* valid request this build does not handle (e.g. size limit)  */
+    GB_ERR_TIMEOUT = 9       /* a bounded device-side wait gave up                          */
+} gb_status;
+
+typedef enum gb_precision {
+    GB_PREC_FP64 = 0,    /* every product in FP64 (the plain reference GPU path)              */
+    GB_PREC_FP16X3 = 1,  /* tensor-core split products hi*hi + hi*lo + lo*hi, FP16 parts,
+                            FP32 accumulation in tensor memory; traces, mu, mu1 in FP64        */
+    GB_PREC_BF16X3 = 2   /* as GB_PREC_FP16X3 with BF16 parts                                  */
+} gb_precision;
+
+/* Square sparse matrix, compressed sparse rows.  [device] arrays.
+ * ptr: n+1 row offsets; idx: column indices, ascending inside each row;
+ * val: values.  Duplicates are not allowed. */
+typedef struct gb_csr {
+    int32_t n;
+    int64_t nnz;
+    const int64_t* ptr;
+    const int32_t* idx;
+    const double* val;
+} gb_csr;
+
+/* Ragged compressed-sparse-column matrix produced by the column collect
+ * (Eq. dCollect): column j holds the rows S_i of the subgraph i whose core
+ * contains j, in ascending order.  [device] arrays sized by the caller:
+ * ptr n+1, idx and val `capacity` entries.  ptr/idx may be NULL for D1 when
+ * they are taken from D (they are identical). */
+typedef struct gb_csc {
+    int32_t n;
+    int64_t nnz;       /* out: entries written                                  */
+    int64_t capacity;  /* in: entries idx/val can hold                          */
+    int64_t* ptr;
+    int32_t* idx;
+    double* val;
+} gb_csc;
+
+/* Undirected graph as a symmetric adjacency (CSR, no self loops, ascending
+ * neighbours).  [device] arrays: ptr n+1, idx `capacity` entries. */
+typedef struct gb_graph {
+    int32_t n;
+    int64_t nnz;       /* out: number of directed edges (twice the undirected count) */
+    int64_t capacity;  /* in: entries idx can hold                                    */
+    int64_t* ptr;
+    int32_t* idx;
+} gb_graph;
+
+/* Core/halo partition.  [device] arrays sized by the caller:
+ *   core_ptr n+1, core_idx n, core_pos n, sub_ptr n+1, sub_idx sub_capacity.
+ * Subgraph i has core  core_idx[core_ptr[i] .. core_ptr[i+1])  (ascending),
+ * vertex set S_i = sub_idx[sub_ptr[i] .. sub_ptr[i+1]) (ascending, core + halo),
+ * and core_pos[k] is the position of core_idx[k] inside S_i. */
+typedef struct gb_partition {
+    int32_t n;
+    int32_t n_sub;         /* out: number of subgraphs                                  */
+    int32_t max_sub;       /* out: largest |S_i|                                        */
+    int32_t max_core;      /* out: largest |core_i|                                     */
+    int64_t sub_nnz;       /* out: sum_i |S_i|                                          */
+    int64_t out_nnz;       /* out: sum_i |S_i| |core_i| = nnz of a collected matrix     */
+    int64_t sub_capacity;  /* in: entries sub_idx can hold                              */
+    int64_t* core_ptr;
+    int32_t* core_idx;
+    int32_t* core_pos;
+    int64_t* sub_ptr;
+    int32_t* sub_idx;
+} gb_partition;
+
+typedef struct gb_opts {
+    int32_t precision;   /* gb_precision                                                  */
+    int32_t max_newton;  /* mu passes (each a full recursion); <= 0 selects 40             */
+    double tol_occ;      /* accept mu when |Tr D - N_occ| <= tol_occ * N_occ;
+                            <= 0 selects 1e-10 (FP64) or 1e-6 (split precision)           */
+    int32_t min_steps;   /* lower bound on recursion steps; <= 0 selects 6                 */
+    int32_t ns_iters;    /* Newton-Schulz corrections per step; <= 0 selects 3 (FP64) / 2 */
+} gb_opts;
+
+typedef struct gb_report {
+    int32_t passes;          /* recursion passes taken by the mu iteration                */
+    int32_t max_steps;       /* largest per-subgraph step count of the final pass         */
+    int32_t n_sub;           /* subgraphs                                                 */
+    int32_t max_sub;         /* largest subgraph                                          */
+    double mu;               /* final chemical potential                                  */
+    double trace_d;          /* sum_i Tr_c d^(i) at mu                                    */
+    double dndmu;            /* beta sum_i Tr_c d^(i)(I - d^(i))                          */
+    double occ_residual;     /* trace_d - N_occ                                           */
+    double trace_d1mu;       /* sum_i Tr_c d1_mu^(i)                                      */
+    double eps_min, eps_max; /* Gershgorin bounds over all subgraphs                      */
+    double gemm_flops;       /* algorithmic flops of the final pass (2 n^3 per product)   */
+    int64_t kernel_launches; /* kernels launched by this call                             */
+} gb_report;
+
+/* ---- handle ------------------------------------------------------------ */
+typedef struct gb_handle gb_handle;
+
+/* Create a handle bound to `stream` (a cudaStream_t; NULL = legacy default
+ * stream) on the current CUDA device.  *h receives the handle.
+ * Errors: GB_ERR_ARG (h NULL), GB_ERR_DEVICE. */
+int gb_create(gb_handle** h, void* stream);
+int gb_destroy(gb_handle* h);
+
+/* Give the handle `bytes` of caller-owned [device] scratch at `dptr` (256-byte
+ * aligned).  The caller keeps ownership and must keep it alive while calls
+ * using the handle are in flight. */
+int gb_set_workspace(gb_handle* h, void* dptr, size_t bytes);
+
+/* Bytes of workspace the last call that returned GB_ERR_WORKSPACE needed. */
+size_t gb_required_workspace(const gb_handle* h);
+
+/* Human-readable name of a status code (static string). */
+const char* gb_status_string(int status);
+
+/* Library version and the compute capability it was built for (e.g. 103). */
+int gb_version(int32_t* major, int32_t* minor, int32_t* arch);
+
+/* ---- gb_graph_build ---------------------------------------------------- *
+ * Estimate the data-dependency graph G (Sec. "Estimating the connectivity
+ * graph"; the numerically thresholded matrices of Sec. "Numerically
+ * thresholded sparse matrix algebra"):
+ *   E = {(i,j): i != j, |H_ij| > tau} U {(i,j): i != j, |D_prev,ij| > tau},
+ * symmetrised; with paths2 != 0 the paths of length two are added, E <- E U E^2
+ * (the paper's favourite estimate with D_prev, or the ad hoc H^2 without).
+ *   H       [device] CSR, n x n.
+ *   D_prev  [device] collected density of a previous step (gb_csc) or NULL.
+ *   tau     strict threshold >= 0.
+ *   G       out; G->ptr, G->idx caller-allocated.  If G->capacity is too small
+ *           the call returns GB_ERR_CAPACITY with G->nnz = required entries.
+ * Output is bit-exact and independent of thread scheduling.
+ * Workspace: gb_graph_build_workspace_size(). */
+size_t gb_graph_build_workspace_size(int32_t n, int64_t nnz_h, int64_t nnz_dprev, int paths2);
+int gb_graph_build(gb_handle* h, const gb_csr* H, const gb_csc* D_prev, double tau,
+                   int paths2, gb_graph* G);
+
+/* ---- gb_partition ------------------------------------------------------ *
+ * Split G into disjoint cores and distance-1 halos (Fig. 1: the halo is the
+ * set of directly connected vertices; Sec. "Choosing the graph partitioning":
+ * multi-vertex cores).
+ *   group   [device] group id per vertex in [0, n_groups) or NULL.  With
+ *           groups, each non-empty group is one core, in ascending group id.
+ *           Without, consecutive blocks of target_core_size vertices.
+ *   P       out (see gb_partition).  GB_ERR_CAPACITY with P->sub_nnz set when
+ *           P->sub_capacity is too small.
+ * Output is bit-exact.  Synchronises the stream (sizes are returned in P).
+ * Workspace: gb_partition_workspace_size(). */
+size_t gb_partition_workspace_size(int32_t n, int64_t nnz_g);
+int gb_partition(gb_handle* h, const gb_graph* G, const int32_t* group, int32_t n_groups,
+                 int32_t target_core_size, gb_partition* P);
+
+/* ---- gb_density_and_response ------------------------------------------- *
+ * For every subgraph i: gather h^(i) = H[S_i,S_i] and h1_r^(i) = H1_r[S_i,S_i]
+ * (Eq. sub_f), evaluate the Fermi-Dirac density matrix
+ *   d^(i) = [exp(beta (h^(i) - mu I)) + I]^-1                       (Eq. Fermi)
+ * with one mu shared by all subgraphs, set by Tr[D_G(mu)] = N_occ = Ne/2 with
+ * core traces and Newton-Raphson steps (Eq. NewtonRaphson) safeguarded by
+ * bisection; the canonical response (Eqs. D1, ddlambda, dddmu, dmu_1)
+ *   d1_lambda^(i) = d/dlambda Theta_beta(mu I - h^(i) - lambda h1^(i)),
+ *   d1_mu^(i) = beta d^(i) (I - d^(i)),
+ *   mu1_r = -sum_i Tr_c d1_lambda^(i) / sum_i Tr_c d1_mu^(i),
+ *   D1_r = {d1_lambda^(i)|_c}_collect + mu1_r {d1_mu^(i)|_c}_collect;
+ * and collect the core columns into D and D1_r (Eq. dCollect).
+ *   H        [host] struct of [device] CSR arrays.
+ *   H1       [host] array of m structs of [device] CSR arrays (m >= 0).
+ *   kT       electronic temperature in eV, > 0.
+ *   n_electrons  Ne; spin-restricted, N_occ = Ne / 2, 0 < N_occ < n.
+ *   P        partition from gb_partition (its [device] arrays).
+ *   opts     [host] options or NULL for defaults.
+ *   mu_inout [host] initial guess on entry (NaN: start from the spectral
+ *            bracket), converged mu on return.
+ *   D        out, [device] arrays with capacity >= P->out_nnz.
+ *   D1       out, [host] array of m gb_csc with [device] val arrays.
+ *   mu1      out, [host] array of m doubles (may be NULL when m == 0).
+ *   rep      out, [host] report or NULL.
+ * The recursion computes d = (I - Z_s)/2 with Z_s = tanh(beta (h - mu)/2) by
+ * s doublings Z <- 2 Z (I + Z^2)^-1 from a Taylor start, and d1_lambda by the
+ * exact derivative of the same recursion.  Split-precision modes require
+ * |S_i| <= 128 (else GB_ERR_UNSUPPORTED); FP64 has no size limit.
+ * Errors: GB_ERR_ARG, GB_ERR_CAPACITY, GB_ERR_WORKSPACE, GB_ERR_MU_BRACKET,
+ * GB_ERR_NO_CONVERGE (outputs hold the last pass), GB_ERR_NAN, GB_ERR_DEVICE,
+ * GB_ERR_UNSUPPORTED, GB_ERR_TIMEOUT.  Synchronises the stream.
+ * Workspace: gb_density_workspace_size(). */
+int gb_density_workspace_size(const gb_partition* P, int32_t m, const gb_opts* opts,
+                              size_t* bytes);
+int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_csr* H1, int32_t m,
+                            double kT, double n_electrons, const gb_partition* P,
+                            const gb_opts* opts, double* mu_inout, gb_csc* D, gb_csc* D1,
+                            double* mu1, gb_report* rep);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBQR_H */
