@@ -1,0 +1,363 @@
+"""Benchmark: orbitals/s for D + D1 on the 60,000-orbital water box.
+
+One step = the whole hot path on one synthetic system: graph_build (thresholded
+H) + partition (one water per core) + density_and_response (Fermi recursion,
+shared mu, canonical response with one H1, collect).  The split-precision
+tensor-core path (FP16 hi/lo parts, FP32 accumulation) is the headline; the
+plain FP64 GPU path is timed beside it on the same input.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+value  = orbitals / second with H, H1 resident in HBM (CUDA events, max over ranks)
+e2e    = the same through the public API from pinned host buffers: H2D of
+         H, H1 and D2H of D, D1, mu, mu1 inside the timed region
+L2 is flushed (512 MB write) before every timed step.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "orbitals/s for D+D1 on 60k-orbital box, mixed vs FP64 path, max|ΔD|≤1e-5"
+WORKLOAD = "water10k"
+CONFIG_TEXT = ("10,000 H2O (60,000 orbitals), periodic box 66.9 A, sp tight binding, kT 0.2 eV, "
+               "graph = |H| > 1e-4, one molecule per core (10,000 subgraphs), one H1")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gbqr", choices=["gbqr", "reference"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--fp64-steps", type=int, default=2)
+    p.add_argument("--companion", default="water10k_kT0.05")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(workload_name: str, budget_s: float = 15.0):
+    """The oracle (graph method, per-subgraph LAPACK eigh) on a bounded sample.
+
+    Sample: the 1,000-water box from the same generator (same kT, tau and
+    subgraph shapes), repeated until about budget_s seconds have passed.
+    """
+    from oracle import graph_build as o_graph, oracle_graph, partition as o_part
+    from synth import WORKLOADS, make_workload
+    from synth.workloads import Workload
+
+    wl_full = WORKLOADS[workload_name]
+    wl = Workload("sample", 1, 1000, wl_full.kT, wl_full.tau)
+    _, system, h1 = make_workload(wl, n_rhs=1)
+    H = system.H
+    workers = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        adj = o_graph(H.n, H.indptr, H.indices, H.data, wl.tau)
+        part = o_part(adj, system.orb_group)
+        oracle_graph(H, h1, wl.kT, system.n_occ, part, workers=workers)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or reps >= 50:
+            break
+    return {"value": reps * H.n / el, "unit": "orbitals/s", "cores": workers, "kind": "oracle",
+            "sample": f"{reps} x oracle graph solve (graph, partition, eigh per subgraph, mu, mu1, collect) "
+                      f"of the 1,000-water box ({H.n} orbitals, kT {wl.kT}, tau {wl.tau}, m=1), "
+                      f"process pool of {workers}", "seconds": el}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world, dist, e2e_steps=0):
+    """Time the whole hot path on one workload; return the measurements."""
+    import numpy as np
+    import torch
+
+    from synth import make_workload
+
+    wl, system, h1 = make_workload(workload, n_rhs=1)
+    H = gb.DeviceCSR.from_arrays(system.H.n, system.H.indptr, system.H.indices, system.H.data, dev)
+    H1 = [gb.DeviceCSR.from_arrays(h.n, h.indptr, h.indices, h.data, dev) for h in h1]
+    groups = torch.as_tensor(system.orb_group, device=dev)
+    n_groups = int(system.orb_group.max()) + 1
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    launches = {"n": 0}
+
+    def step(precision, mu0, Hs=H, H1s=H1, max_newton=0):
+        G = gb.graph_build(Hs, wl.tau, handle=handle)
+        launches["n"] += handle.lib.gb_launch_count(handle.h)
+        P = gb.partition(G, groups, n_groups, handle=handle)
+        launches["n"] += handle.lib.gb_launch_count(handle.h)
+        R = gb.density_and_response(Hs, H1s, wl.kT, system.n_electrons, P, precision=precision, mu0=mu0,
+                                    handle=handle, max_newton=max_newton, raise_on_error=max_newton == 0)
+        launches["n"] += R.report["kernel_launches"]
+        return P, R
+
+    def timed(precision, k, w, mu0):
+        for _ in range(w):
+            P, R = step(precision, mu0)
+            mu0 = R.mu
+        times, kms, passes, flops = [], [], [], []
+        launches["n"] = 0
+        for _ in range(k):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            if world > 1:
+                dist.barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P, R = step(precision, mu0)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            times.append(e0.elapsed_time(e1))
+            kms.append(R.report["pass_kernel_ms"])
+            passes.append(R.report["passes"])
+            flops.append(R.report["gemm_flops"])
+            mu0 = R.mu
+        return P, R, times, kms, passes, flops, launches["n"]
+
+    out = {"workload": workload, "wl": wl, "system": system}
+    # split precision (FP16 parts): cold start for mu, then warm-started steps
+    _, R0, _, _, _, _, _ = timed("fp16x3", 0, max(warmup, 3), math.nan)
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    P, Rm, t_m, k_m, pass_m, fl_m, n_launch = timed("fp16x3", steps, 0, R0.mu)
+    out["clocks"] = clocks.stop()
+    t_step = statistics.mean(t_m)
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    out.update(P=P, ms=t_step, value=world * system.n_orb / (t_step / 1e3), launches=n_launch,
+               passes=pass_m[-1], max_steps=Rm.report["max_steps"], mu=Rm.mu, mu1=Rm.mu1[0],
+               kernel_ms=statistics.mean(k / p for k, p in zip(k_m, pass_m)),
+               flops=statistics.mean(fl_m))
+    Dm, D1m = Rm.D.val.clone(), Rm.D1[0].val.clone()
+
+    if e2e_steps:
+        # public API from pinned host buffers: H2D of H, H1 and D2H of D, D1 inside the region
+        hp = [torch.as_tensor(a).pin_memory() for a in (system.H.indptr, system.H.indices.astype(np.int32),
+                                                        system.H.data)]
+        h1p = [torch.as_tensor(a).pin_memory() for a in (h1[0].indptr, h1[0].indices.astype(np.int32),
+                                                         h1[0].data)]
+        host_out = [torch.empty(P.out_nnz, dtype=torch.float64).pin_memory() for _ in range(2)]
+        bi = sum(t.numel() * t.element_size() for t in hp + h1p)
+        bo = 2 * P.out_nnz * 8
+        ts_e2e, mu_e = [], Rm.mu
+        for it in range(e2e_steps + 1):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            Hd = gb.DeviceCSR(system.n_orb, *[t.to(dev, non_blocking=True) for t in hp])
+            H1d = [gb.DeviceCSR(system.n_orb, *[t.to(dev, non_blocking=True) for t in h1p])]
+            _, Re = step("fp16x3", mu_e, Hs=Hd, H1s=H1d)
+            host_out[0].copy_(Re.D.val, non_blocking=True)
+            host_out[1].copy_(Re.D1[0].val, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            mu_e = Re.mu
+            if it > 0:
+                ts_e2e.append(e0.elapsed_time(e1))
+        ms_e2e = statistics.mean(ts_e2e)
+        out["e2e"] = {"value": world * system.n_orb / (ms_e2e / 1e3), "unit": "orbitals/s",
+                      "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": ms_e2e}
+
+    # the plain FP64 GPU path on the same input (its own mu), and both paths at one mu
+    _, R64, t64, k64, pass64, _, _ = timed("fp64", fp64_steps, 1, Rm.mu)
+    out["fp64"] = {"value": system.n_orb / (statistics.mean(t64) / 1e3), "unit": "orbitals/s",
+                   "ms_per_step": statistics.mean(t64), "passes": pass64[-1],
+                   "kernel_ms": statistics.mean(k64), "mu": R64.mu}
+    _, Rs = step("fp16x3", R64.mu, max_newton=1)
+    out["accuracy_vs_fp64_gpu"] = {
+        "max_abs_dD": float((Dm - R64.D.val).abs().max().item()),
+        "max_abs_dD1": float((D1m - R64.D1[0].val).abs().max().item()),
+        "dmu": Rm.mu - R64.mu, "dmu1": Rm.mu1[0] - R64.mu1[0],
+        "at_fp64_mu": {"max_abs_dD": float((Rs.D.val - R64.D.val).abs().max().item()),
+                       "max_abs_dD1": float((Rs.D1[0].val - R64.D1[0].val).abs().max().item())}}
+    return out
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2212_01997_gb300 as gb
+    from paper_2212_01997_gb300 import build as gbuild
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    if rank == 0:
+        gbuild.build()
+    if world > 1:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    handle = gb.Handle(stream, dev)
+
+    head = measure(gb, args.workload, args.steps, args.warmup, args.fp64_steps, dev, stream, handle, world,
+                   dist, e2e_steps=max(2, args.steps // 2))
+    comp = None
+    if args.companion:
+        comp = measure(gb, args.companion, max(2, args.steps // 2), 2, 1, dev, stream, handle, world, dist)
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = peaks.get("bf16_tflops", 1900.0)
+    achieved = head["flops"] / (head["kernel_ms"] / 1e3) / 1e12
+    roof = {"bound": "tensor", "kernel": "k_fermi_split", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": ("measured bf16 dense burst (MEASURED_PEAKS.json); the fp16 dense rate is the "
+                            "same nominal figure" if "bf16_tflops" in peaks else "fallback 1.9 PFLOP/s bf16"),
+            "kernel_ms_per_launch": head["kernel_ms"], "algorithmic_flops_per_launch": head["flops"],
+            "flop_count": "2 |S_i|^3 per matrix product of the recursion, summed over subgraphs; the three "
+                          "split passes and the padding to 128 rows are not counted"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload)
+
+    if rank == 0:
+        wl, system = head["wl"], head["system"]
+        line = {
+            "metric": METRIC, "value": head["value"], "unit": "orbitals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16x3-f32acc", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {workload_text(wl, system)}",
+                       "n_orbitals": system.n_orb, "n_subgraphs": head["P"].n_sub,
+                       "max_subgraph": head["P"].max_sub, "m": 1, "kT": wl.kT, "tau": wl.tau,
+                       "l2": "flushed (512 MB write) before every timed step",
+                       "parallelism": f"replicas x{world} (independent systems, no collective)",
+                       "step": "graph_build + partition + density_and_response (warm-started mu)"},
+            "e2e": head.get("e2e"), "gpu_launches": head["launches"], "roofline": roof, "cpu_baseline": cpu,
+            "clocks": head["clocks"], "fp64_path": head["fp64"],
+            "mixed_over_fp64": head["value"] / world / head["fp64"]["value"],
+            "accuracy_vs_fp64_gpu": head["accuracy_vs_fp64_gpu"],
+            "mu": head["mu"], "mu1": head["mu1"], "passes": head["passes"], "max_steps": head["max_steps"],
+        }
+        if comp is not None:
+            cwl, csys = comp["wl"], comp["system"]
+            line["companion"] = {
+                "workload": f"{args.companion}: {workload_text(cwl, csys)}", "value": comp["value"],
+                "unit": "orbitals/s", "ms_per_step": comp["ms"], "fp64_path": comp["fp64"],
+                "mixed_over_fp64": comp["value"] / world / comp["fp64"]["value"],
+                "accuracy_vs_fp64_gpu": comp["accuracy_vs_fp64_gpu"], "clocks": comp["clocks"],
+                "max_steps": comp["max_steps"]}
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def workload_text(wl, system):
+    return (f"{system.meta.get('n_waters')} H2O ({system.n_orb} orbitals), periodic box "
+            f"{system.box:.1f} A, sp tight binding, kT {wl.kT} eV, graph = |H| > {wl.tau:g}, one molecule "
+            f"per core, one H1")
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands on the host cores, on bounded samples of the workload."""
+    if rank != 0:
+        return
+    samples = []
+    t_all = time.perf_counter()
+    for _ in range(args.warmup):
+        cpu_baseline(args.workload, budget_s=2.0)
+    for _ in range(args.steps):
+        samples.append(cpu_baseline(args.workload, budget_s=8.0))
+    value = statistics.mean(s["value"] for s in samples)
+    ms = statistics.mean(1e3 * s["seconds"] for s in samples)
+    line = {"metric": METRIC, "value": value, "unit": "orbitals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{args.workload}: {CONFIG_TEXT}",
+                       "sample": samples[0]["sample"]},
+            "cpu_baseline": {"value": value, "unit": "orbitals/s", "cores": samples[0]["cores"],
+                             "kind": "oracle", "sample": samples[0]["sample"]},
+            "e2e": {"value": value, "unit": "orbitals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t_all}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

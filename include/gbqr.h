@@ -92,7 +92,7 @@ typedef struct gb_graph {
  * Subgraph i has core  core_idx[core_ptr[i] .. core_ptr[i+1])  (ascending),
  * vertex set S_i = sub_idx[sub_ptr[i] .. sub_ptr[i+1]) (ascending, core + halo),
  * and core_pos[k] is the position of core_idx[k] inside S_i. */
-typedef struct gb_partition {
+typedef struct gb_part {
     int32_t n;
     int32_t n_sub;         /* out: number of subgraphs                                  */
     int32_t max_sub;       /* out: largest |S_i|                                        */
@@ -105,15 +105,22 @@ typedef struct gb_partition {
     int32_t* core_pos;
     int64_t* sub_ptr;
     int32_t* sub_idx;
-} gb_partition;
+} gb_part;
 
 typedef struct gb_opts {
     int32_t precision;   /* gb_precision                                                  */
     int32_t max_newton;  /* mu passes (each a full recursion); <= 0 selects 40             */
-    double tol_occ;      /* accept mu when |Tr D - N_occ| <= tol_occ * N_occ;
-                            <= 0 selects 1e-10 (FP64) or 1e-6 (split precision)           */
+    double tol_occ;      /* also accept mu when |Tr D - N_occ| <= tol_occ * N_occ
+                            (<= 0: this test is off)                                       */
     int32_t min_steps;   /* lower bound on recursion steps; <= 0 selects 6                 */
     int32_t ns_iters;    /* Newton-Schulz corrections per step; <= 0 selects 3 (FP64) / 2 */
+    double tol_d;        /* accept mu when the remaining Newton step |dmu| = |Tr D - N_occ|
+                            / (dTr D / dmu) would change no element of D by more than
+                            tol_d, using |dD_jk| <= |dmu| max diag(beta d (I - d)) (d1_mu is
+                            positive semidefinite).  <= 0 selects 1e-11 (FP64) / 1e-6 (split).
+                            When a Newton step no longer halves the residual (trace
+                            round-off floor) mu is accepted: always in split precision,
+                            in FP64 once that bound is within 10 tol_d.                     */
 } gb_opts;
 
 typedef struct gb_report {
@@ -127,7 +134,11 @@ typedef struct gb_report {
     double occ_residual;     /* trace_d - N_occ                                           */
     double trace_d1mu;       /* sum_i Tr_c d1_mu^(i)                                      */
     double eps_min, eps_max; /* Gershgorin bounds over all subgraphs                      */
-    double gemm_flops;       /* algorithmic flops of the final pass (2 n^3 per product)   */
+    double gemm_flops;       /* algorithmic flops of one pass: 2 |S_i|^3 per matrix product,
+                                summed over the products the recursion performs            */
+    double pass_kernel_ms;   /* device time of the recursion kernel, summed over passes
+                                (CUDA events on the handle's stream)                       */
+    double mu_d_bound;       /* bound on the change of D the remaining mu step would make */
     int64_t kernel_launches; /* kernels launched by this call                             */
 } gb_report;
 
@@ -147,6 +158,9 @@ int gb_set_workspace(gb_handle* h, void* dptr, size_t bytes);
 
 /* Bytes of workspace the last call that returned GB_ERR_WORKSPACE needed. */
 size_t gb_required_workspace(const gb_handle* h);
+
+/* Kernels launched by the most recent call made with this handle. */
+int64_t gb_launch_count(const gb_handle* h);
 
 /* Human-readable name of a status code (static string). */
 const char* gb_status_string(int status);
@@ -179,13 +193,13 @@ int gb_graph_build(gb_handle* h, const gb_csr* H, const gb_csc* D_prev, double t
  *   group   [device] group id per vertex in [0, n_groups) or NULL.  With
  *           groups, each non-empty group is one core, in ascending group id.
  *           Without, consecutive blocks of target_core_size vertices.
- *   P       out (see gb_partition).  GB_ERR_CAPACITY with P->sub_nnz set when
+ *   P       out (see gb_part).  GB_ERR_CAPACITY with P->sub_nnz set when
  *           P->sub_capacity is too small.
  * Output is bit-exact.  Synchronises the stream (sizes are returned in P).
- * Workspace: gb_partition_workspace_size(). */
-size_t gb_partition_workspace_size(int32_t n, int64_t nnz_g);
+ * Workspace: gb_partition_workspace_size() (n_groups <= 0: blocks). */
+size_t gb_partition_workspace_size(int32_t n, int64_t nnz_g, int32_t n_groups);
 int gb_partition(gb_handle* h, const gb_graph* G, const int32_t* group, int32_t n_groups,
-                 int32_t target_core_size, gb_partition* P);
+                 int32_t target_core_size, gb_part* P);
 
 /* ---- gb_density_and_response ------------------------------------------- *
  * For every subgraph i: gather h^(i) = H[S_i,S_i] and h1_r^(i) = H1_r[S_i,S_i]
@@ -219,10 +233,10 @@ int gb_partition(gb_handle* h, const gb_graph* G, const int32_t* group, int32_t 
  * GB_ERR_NO_CONVERGE (outputs hold the last pass), GB_ERR_NAN, GB_ERR_DEVICE,
  * GB_ERR_UNSUPPORTED, GB_ERR_TIMEOUT.  Synchronises the stream.
  * Workspace: gb_density_workspace_size(). */
-int gb_density_workspace_size(const gb_partition* P, int32_t m, const gb_opts* opts,
+int gb_density_workspace_size(const gb_part* P, int32_t m, const gb_opts* opts,
                               size_t* bytes);
 int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_csr* H1, int32_t m,
-                            double kT, double n_electrons, const gb_partition* P,
+                            double kT, double n_electrons, const gb_part* P,
                             const gb_opts* opts, double* mu_inout, gb_csc* D, gb_csc* D1,
                             double* mu1, gb_report* rep);
 

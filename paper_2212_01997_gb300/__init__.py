@@ -1,0 +1,257 @@
+"""GB300-native graph-based density matrix and canonical response.
+
+Thin Python binding over the C ABI of ``libgbqr.so`` (include/gbqr.h): the
+functions below only marshal torch device tensors into the C structs and grow
+caller-owned workspaces; every step of the computation runs in the CUDA
+kernels of the library.  PyTorch provides device memory and the stream.
+
+    G = graph_build(H, tau, paths2=False, d_prev=None)
+    P = partition(G, groups=orbital_molecule_ids, n_groups=n_molecules)
+    R = density_and_response(H, [H1], kT, n_electrons, P, precision="fp16x3")
+    R.D, R.D1[0], R.mu, R.mu1[0]
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import math
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _lib as L
+from ._lib import GbError, PRECISION
+
+__all__ = ["DeviceCSR", "Graph", "Partition", "CSC", "Result", "Handle", "graph_build", "partition",
+           "density_and_response", "GbError", "PRECISION", "library"]
+
+
+def library():
+    """The loaded libgbqr.so (raises if it has not been built)."""
+    return L.load()
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+@dataclass
+class DeviceCSR:
+    """Square CSR matrix on the GPU: ptr int64 (n+1), idx int32, val float64."""
+
+    n: int
+    ptr: torch.Tensor
+    idx: torch.Tensor
+    val: torch.Tensor
+
+    @staticmethod
+    def from_arrays(n, indptr, indices, data, device="cuda") -> "DeviceCSR":
+        return DeviceCSR(int(n), torch.as_tensor(indptr, dtype=torch.int64).to(device),
+                         torch.as_tensor(indices, dtype=torch.int32).to(device),
+                         torch.as_tensor(data, dtype=torch.float64).to(device))
+
+    @property
+    def nnz(self) -> int:
+        return int(self.idx.numel())
+
+    def struct(self) -> L.gb_csr:
+        return L.gb_csr(self.n, self.nnz, _ptr(self.ptr), _ptr(self.idx), _ptr(self.val))
+
+
+@dataclass
+class Graph:
+    n: int
+    ptr: torch.Tensor
+    idx: torch.Tensor
+
+    @property
+    def nnz(self) -> int:
+        return int(self.idx.numel())
+
+    def struct(self) -> L.gb_graph:
+        return L.gb_graph(self.n, self.nnz, self.nnz, _ptr(self.ptr), _ptr(self.idx))
+
+
+@dataclass
+class Partition:
+    n: int
+    n_sub: int
+    max_sub: int
+    max_core: int
+    sub_nnz: int
+    out_nnz: int
+    core_ptr: torch.Tensor
+    core_idx: torch.Tensor
+    core_pos: torch.Tensor
+    sub_ptr: torch.Tensor
+    sub_idx: torch.Tensor
+
+    def struct(self) -> L.gb_part:
+        return L.gb_part(self.n, self.n_sub, self.max_sub, self.max_core, self.sub_nnz, self.out_nnz,
+                         self.sub_idx.numel(), _ptr(self.core_ptr), _ptr(self.core_idx),
+                         _ptr(self.core_pos), _ptr(self.sub_ptr), _ptr(self.sub_idx))
+
+
+@dataclass
+class CSC:
+    """Collected ragged CSC matrix: column j holds rows S_i of its subgraph."""
+
+    n: int
+    ptr: torch.Tensor
+    idx: torch.Tensor
+    val: torch.Tensor
+
+    def struct(self, with_index=True) -> L.gb_csc:
+        return L.gb_csc(self.n, self.val.numel(), self.val.numel(),
+                        _ptr(self.ptr) if with_index else None,
+                        _ptr(self.idx) if with_index else None, _ptr(self.val))
+
+
+@dataclass
+class Result:
+    mu: float
+    mu1: list
+    D: CSC
+    D1: list
+    status: int
+    report: dict = field(default_factory=dict)
+
+
+class Handle:
+    """A gb_handle bound to one CUDA stream, with a growable workspace."""
+
+    def __init__(self, stream: torch.cuda.Stream | None = None, device=None):
+        self.lib = L.load()
+        self.device = torch.device(device or "cuda")
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            L.check("gb_create", self.lib.gb_create(C.byref(h), C.c_void_p(self.stream.cuda_stream)))
+        self.h = h
+        self.ws = None
+
+    def workspace(self, nbytes: int) -> None:
+        nbytes = max(int(nbytes), 256)
+        if self.ws is None or self.ws.numel() < nbytes:
+            self.ws = torch.empty(int(nbytes * 1.05) + 4096, dtype=torch.uint8, device=self.device)
+        L.check("gb_set_workspace", self.lib.gb_set_workspace(self.h, self.ws.data_ptr(), self.ws.numel()))
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) and self.h.value:
+                self.lib.gb_destroy(self.h)
+        except Exception:
+            pass
+
+
+_handles: dict = {}
+
+
+def _default_handle(device=None) -> Handle:
+    dev = torch.device(device or "cuda")
+    stream = torch.cuda.current_stream(dev)
+    key = (dev.index, stream.cuda_stream)
+    if key not in _handles:
+        _handles[key] = Handle(stream, dev)
+    return _handles[key]
+
+
+def graph_build(H: DeviceCSR, tau: float, *, paths2: bool = False, d_prev: CSC | None = None,
+                handle: Handle | None = None) -> Graph:
+    """gb_graph_build: thresholded, symmetrised graph (+ paths of length two)."""
+    hd = handle or _default_handle(H.ptr.device)
+    lib = hd.lib
+    nnz_d = 0 if d_prev is None else d_prev.val.numel()
+    hd.workspace(lib.gb_graph_build_workspace_size(H.n, H.nnz, nnz_d, int(paths2)))
+    cap = max(1, 2 * (H.nnz + nnz_d) * (8 if paths2 else 1))
+    hs = H.struct()
+    ds = None if d_prev is None else C.byref(d_prev.struct())
+    for _ in range(3):
+        ptr = torch.empty(H.n + 1, dtype=torch.int64, device=hd.device)
+        idx = torch.empty(cap, dtype=torch.int32, device=hd.device)
+        g = L.gb_graph(H.n, 0, cap, ptr.data_ptr(), idx.data_ptr())
+        st = lib.gb_graph_build(hd.h, C.byref(hs), ds, float(tau), int(paths2), C.byref(g))
+        if st == 2:  # GB_ERR_CAPACITY
+            cap = int(g.nnz) + 1
+            continue
+        L.check("gb_graph_build", st)
+        return Graph(H.n, ptr, idx[: g.nnz])
+    raise GbError("gb_graph_build", 2)
+
+
+def partition(G: Graph, groups: torch.Tensor | None = None, n_groups: int | None = None, *,
+              target_core_size: int = 6, handle: Handle | None = None) -> Partition:
+    """gb_partition: disjoint cores (one per group id, or blocks) and distance-1 halos."""
+    hd = handle or _default_handle(G.ptr.device)
+    lib = hd.lib
+    n = G.n
+    dev = hd.device
+    if groups is not None:
+        groups = groups.to(device=dev, dtype=torch.int32).contiguous()
+        if n_groups is None:
+            n_groups = int(groups.max().item()) + 1
+    hd.workspace(lib.gb_partition_workspace_size(n, G.nnz, int(n_groups or 0) if groups is not None else 0))
+    core_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    core_idx = torch.empty(n, dtype=torch.int32, device=dev)
+    core_pos = torch.empty(n, dtype=torch.int32, device=dev)
+    sub_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    cap = max(1, G.nnz + n)
+    gs = G.struct()
+    for _ in range(3):
+        sub_idx = torch.empty(cap, dtype=torch.int32, device=dev)
+        p = L.gb_part(n, 0, 0, 0, 0, 0, cap, core_ptr.data_ptr(), core_idx.data_ptr(),
+                      core_pos.data_ptr(), sub_ptr.data_ptr(), sub_idx.data_ptr())
+        st = lib.gb_partition(hd.h, C.byref(gs), None if groups is None else groups.data_ptr(),
+                              int(n_groups or 0), int(target_core_size), C.byref(p))
+        if st == 2:
+            cap = int(p.sub_nnz) + 1
+            continue
+        L.check("gb_partition", st)
+        return Partition(n, p.n_sub, p.max_sub, p.max_core, p.sub_nnz, p.out_nnz,
+                         core_ptr[: p.n_sub + 1], core_idx, core_pos, sub_ptr[: p.n_sub + 1],
+                         sub_idx[: p.sub_nnz])
+    raise GbError("gb_partition", 2)
+
+
+def density_and_response(H: DeviceCSR, H1: list, kT: float, n_electrons: float, part: Partition, *,
+                         precision: str = "fp64", mu0: float = math.nan, max_newton: int = 0,
+                         tol_occ: float = 0.0, min_steps: int = 0, ns_iters: int = 0, tol_d: float = 0.0,
+                         out: tuple | None = None, handle: Handle | None = None,
+                         raise_on_error: bool = True) -> Result:
+    """gb_density_and_response: D, D1, mu, mu1 on the partitioned graph.
+
+    ``out`` may pass preallocated (D, [D1...]) CSC containers to reuse.
+    """
+    hd = handle or _default_handle(H.ptr.device)
+    lib = hd.lib
+    m = len(H1)
+    opts = L.gb_opts(PRECISION[precision], int(max_newton), float(tol_occ), int(min_steps), int(ns_iters),
+                     float(tol_d))
+    ps = part.struct()
+    nbytes = C.c_size_t()
+    L.check("gb_density_workspace_size", lib.gb_density_workspace_size(C.byref(ps), m, C.byref(opts),
+                                                                         C.byref(nbytes)))
+    hd.workspace(nbytes.value)
+    dev = hd.device
+    if out is None:
+        D = CSC(part.n, torch.empty(part.n + 1, dtype=torch.int64, device=dev),
+                torch.empty(part.out_nnz, dtype=torch.int32, device=dev),
+                torch.empty(part.out_nnz, dtype=torch.float64, device=dev))
+        D1 = [CSC(part.n, D.ptr, D.idx, torch.empty(part.out_nnz, dtype=torch.float64, device=dev))
+              for _ in range(m)]
+    else:
+        D, D1 = out
+    hs = H.struct()
+    h1s = (L.gb_csr * max(m, 1))(*[h.struct() for h in H1])
+    ds = D.struct()
+    d1s = (L.gb_csc * max(m, 1))(*[d.struct(with_index=False) for d in D1])
+    mu = C.c_double(mu0)
+    mu1 = (C.c_double * max(m, 1))()
+    rep = L.gb_report()
+    st = lib.gb_density_and_response(hd.h, C.byref(hs), h1s, m, float(kT), float(n_electrons),
+                                     C.byref(ps), C.byref(opts), C.byref(mu), C.byref(ds), d1s, mu1,
+                                     C.byref(rep))
+    if raise_on_error:
+        L.check("gb_density_and_response", st)
+    report = {k: getattr(rep, k) for k, _ in L.gb_report._fields_}
+    return Result(mu.value, [mu1[r] for r in range(m)], D, D1, st, report)

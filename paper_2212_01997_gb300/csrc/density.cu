@@ -1,0 +1,634 @@
+// gb_density_and_response: gather, spectral bounds, the Fermi recursion and
+// its response per subgraph, the shared chemical potential, the global mu_1
+// and the column collect.
+//
+// Per subgraph i (h = H[S_i, S_i], Eq. sub_f):
+//   d = [exp(beta (h - mu)) + 1]^-1 = (I - Z_s) / 2,  Z_s = tanh(beta (h - mu) / 2)
+// from x0 = beta (h - mu) / 2^(s+1) by a Taylor start Z_0 = x0 (1 - x0^2/3 +
+// 2 x0^4/15) and s doublings Z <- 2 Z (I + Z^2)^-1 (tanh(2y) = 2 tanh y /
+// (1 + tanh^2 y)); the inverse uses the degree-2 Chebyshev start
+// X = (98 I - 80 Y + 32 Y^2)/99 (Y = Z^2, spectrum of I + Y in [1, 2]) and
+// Newton-Schulz corrections X <- X + X R, R = I - (I + Y) X.
+// The grand-canonical response (Eq. ddlambda) is the exact derivative of the
+// same recursion along h1: Z1 <- 2 X Z1 X - (1/2) W Z1 W with W = 2 X Z, and
+// d1_lambda = -Z1_s / 2;  d1_mu = beta d (I - d) = beta (I - Z_s^2) / 4
+// (Eq. dddmu).  mu follows Eq. NewtonRaphson on the core traces, mu_1 Eq. dmu_1.
+#include <math.h>
+#include <string.h>
+
+#include "density.cuh"
+
+namespace {
+
+constexpr int FP64_THREADS = 256;
+constexpr int TS = 32;         // FP64 GEMM tile
+constexpr int NBUF = 7;        // work buffers of the FP64 kernel
+
+// ---------------------------------------------------------------------------
+// collected-matrix structure: column j holds the rows S_i of its subgraph
+// ---------------------------------------------------------------------------
+__global__ void k_csc_lengths(int32_t n_sub, const int64_t* sub_ptr, const int64_t* core_ptr,
+                              const int32_t* core_idx, int64_t* len) {
+    for (int32_t i = blockIdx.x; i < n_sub; i += gridDim.x) {
+        int64_t ni = sub_ptr[i + 1] - sub_ptr[i];
+        for (int64_t e = core_ptr[i] + threadIdx.x; e < core_ptr[i + 1]; e += blockDim.x)
+            len[core_idx[e]] = ni;
+    }
+}
+
+__global__ void k_csc_rows(int32_t n_sub, const int64_t* sub_ptr, const int32_t* sub_idx,
+                           const int64_t* core_ptr, const int32_t* core_idx, const int64_t* col_ptr,
+                           int32_t* row_idx) {
+    for (int32_t i = blockIdx.x; i < n_sub; i += gridDim.x) {
+        const int64_t s0 = sub_ptr[i];
+        const int ni = (int)(sub_ptr[i + 1] - s0);
+        for (int64_t e = core_ptr[i]; e < core_ptr[i + 1]; ++e) {
+            int32_t* dst = row_idx + col_ptr[core_idx[e]];
+            for (int r = threadIdx.x; r < ni; r += blockDim.x) dst[r] = sub_idx[s0 + r];
+        }
+    }
+}
+
+__device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int32_t v) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// input checks and Gershgorin bounds of every principal submatrix
+// ---------------------------------------------------------------------------
+__global__ void k_check_finite(int64_t nnz, const double* v, int* err) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+         e += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(v[e])) set_error(err, GB_ERR_NAN);
+}
+
+__global__ void k_gershgorin(int32_t n_sub, const int64_t* sub_ptr, const int32_t* sub_idx,
+                             const int64_t* Hptr, const int32_t* Hidx, const double* Hval,
+                             double* eps_lo, double* eps_hi) {
+    __shared__ double slo[FP64_THREADS], shi[FP64_THREADS];
+    for (int32_t i = blockIdx.x; i < n_sub; i += gridDim.x) {
+        const int32_t* S = sub_idx + sub_ptr[i];
+        const int n = (int)(sub_ptr[i + 1] - sub_ptr[i]);
+        double lo = INFINITY, hi = -INFINITY;
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+            const int32_t g = S[r];
+            double diag = 0.0, rad = 0.0;
+            for (int64_t p = Hptr[g]; p < Hptr[g + 1]; ++p) {
+                int32_t c = Hidx[p];
+                int lc = lower_bound_i32(S, n, c);
+                if (lc < n && S[lc] == c) {
+                    if (lc == r) diag = Hval[p]; else rad += fabs(Hval[p]);
+                }
+            }
+            lo = fmin(lo, diag - rad);
+            hi = fmax(hi, diag + rad);
+        }
+        slo[threadIdx.x] = lo;
+        shi[threadIdx.x] = hi;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) {
+                slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + o]);
+                shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + o]);
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            eps_lo[i] = slo[0];
+            eps_hi[i] = shi[0];
+        }
+        __syncthreads();
+    }
+}
+
+// Single-block reduction in a fixed order (deterministic): sums of the
+// per-subgraph trace slots, min of eps_lo and max of eps_hi.
+__global__ void k_reduce(int32_t n_sub, int32_t stride, const double* tr, const double* eps_lo,
+                         const double* eps_hi, double* sums, double* bounds) {
+    __shared__ double sh[FP64_THREADS];
+    for (int k = 0; k < stride + 2; ++k) {
+        // 0: sum, 1: min, 2: max
+        const int op = (k < stride) ? (k == TR_MAXW ? 2 : 0) : (k == stride ? 1 : 2);
+        double v = op == 0 ? 0.0 : (op == 1 ? INFINITY : -INFINITY);
+        for (int32_t i = threadIdx.x; i < n_sub; i += blockDim.x) {
+            const double x = k < stride ? tr[(int64_t)i * stride + k] : (k == stride ? eps_lo[i] : eps_hi[i]);
+            v = op == 0 ? v + x : (op == 1 ? fmin(v, x) : fmax(v, x));
+        }
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) {
+                double a = sh[threadIdx.x], b = sh[threadIdx.x + o];
+                sh[threadIdx.x] = op == 0 ? a + b : (op == 1 ? fmin(a, b) : fmax(a, b));
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            if (k < stride) sums[k] = sh[0];
+            else bounds[k - stride] = sh[0];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_d1_fixup(int64_t nnz, double mu1, const double* d1mu, double* d1) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+         e += (int64_t)gridDim.x * blockDim.x)
+        d1[e] += mu1 * d1mu[e];
+}
+
+// ---------------------------------------------------------------------------
+// FP64 path: one block per subgraph, dense n x n blocks in global memory
+// ---------------------------------------------------------------------------
+struct GemmSmem {
+    double a[TS][TS + 1];
+    double b[TS][TS + 1];
+};
+
+// C = alpha A B + beta C0 + gamma I  (row-major n x n; C must not alias A, B;
+// C0 may alias C).
+__device__ void dgemm(int n, double alpha, const double* A, const double* B, double beta,
+                      const double* C0, double gamma, double* C, GemmSmem& sm) {
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int nt = (n + TS - 1) / TS;
+    for (int tile = 0; tile < nt * nt; ++tile) {
+        const int r0 = (tile / nt) * TS, c0 = (tile % nt) * TS;
+        double acc00 = 0.0, acc01 = 0.0, acc10 = 0.0, acc11 = 0.0;
+        for (int k0 = 0; k0 < n; k0 += TS) {
+            for (int e = tid; e < TS * TS; e += FP64_THREADS) {
+                const int rr = e / TS, kk = e % TS;
+                sm.a[rr][kk] = (r0 + rr < n && k0 + kk < n) ? A[(int64_t)(r0 + rr) * n + k0 + kk] : 0.0;
+                sm.b[rr][kk] = (k0 + rr < n && c0 + kk < n) ? B[(int64_t)(k0 + rr) * n + c0 + kk] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int kk = 0; kk < TS; ++kk) {
+                const double a0 = sm.a[ty][kk], a1 = sm.a[ty + 16][kk];
+                const double b0 = sm.b[kk][tx], b1 = sm.b[kk][tx + 16];
+                acc00 = fma(a0, b0, acc00);
+                acc01 = fma(a0, b1, acc01);
+                acc10 = fma(a1, b0, acc10);
+                acc11 = fma(a1, b1, acc11);
+            }
+            __syncthreads();
+        }
+        const double acc[2][2] = {{acc00, acc01}, {acc10, acc11}};
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int r = r0 + ty + 16 * a, c = c0 + tx + 16 * b;
+                if (r < n && c < n) {
+                    const int64_t o = (int64_t)r * n + c;
+                    double v = alpha * acc[a][b];
+                    if (beta != 0.0) v += beta * C0[o];
+                    if (r == c) v += gamma;
+                    C[o] = v;
+                }
+            }
+    }
+    __syncthreads();
+}
+
+// out = scale * (M[S, S] - shift I), M given in CSR
+__device__ void gather_scaled(int n, const int32_t* S, const int64_t* ptr, const int32_t* idx,
+                              const double* val, double scale, double shift, double* out) {
+    for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) out[e] = 0.0;
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        const int32_t g = S[r];
+        for (int64_t p = ptr[g]; p < ptr[g + 1]; ++p) {
+            const int32_t c = idx[p];
+            const int lc = lower_bound_i32(S, n, c);
+            if (lc < n && S[lc] == c) out[(int64_t)r * n + lc] = scale * val[p];
+        }
+        out[(int64_t)r * n + r] -= scale * shift;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(FP64_THREADS) k_fermi_fp64(PassArgs a) {
+    __shared__ GemmSmem sm;
+    __shared__ double red[FP64_THREADS];
+    for (int32_t i = blockIdx.x; i < a.n_sub; i += gridDim.x) {
+        const int64_t s0 = a.sub_ptr[i];
+        const int n = (int)(a.sub_ptr[i + 1] - s0);
+        const int32_t* S = a.sub_idx + s0;
+        const int64_t base = a.moff[i];
+        double* B[NBUF];
+#pragma unroll
+        for (int k = 0; k < NBUF; ++k) B[k] = a.pool + (int64_t)k * a.pool_stride + base;
+        double* Z1[GB_MAX_RHS];
+        for (int r = 0; r < a.m; ++r) Z1[r] = a.pool + (int64_t)(NBUF + r) * a.pool_stride + base;
+
+        int s = recursion_steps(a.beta, a.mu, a.eps_lo[i], a.eps_hi[i], a.min_steps);
+        double alpha = ldexp(a.beta, -(s + 1));
+        double *x0 = B[0], *Q = B[1], *P = B[2], *Z = B[3];
+        // Taylor start: Z0 = x0 (I - Q/3 + 2 Q^2/15), Q = x0^2
+        gather_scaled(n, S, a.Hptr, a.Hidx, a.Hval, alpha, a.mu, x0);
+        dgemm(n, 1.0, x0, x0, 0.0, nullptr, 0.0, Q, sm);
+        {
+            // rho(x0)^2 <= max_r sum_c |Q_rc|: drop k steps while 2^k x0 stays
+            // within spectral radius 1 (x0 scales by 2^k, Q by 4^k, exactly)
+            double rs = 0.0;
+            for (int r = threadIdx.x; r < n; r += blockDim.x) {
+                double t = 0.0;
+                for (int c = 0; c < n; ++c) t += fabs(Q[(int64_t)r * n + c]);
+                rs = fmax(rs, t);
+            }
+            red[threadIdx.x] = rs;
+            __syncthreads();
+            for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+                if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+                __syncthreads();
+            }
+            const double qmax = red[0];
+            __syncthreads();
+            int k = 0;
+            while (k < s - a.min_steps && qmax * ldexp(1.0, 2 * (k + 1)) <= 1.0) ++k;
+            if (k > 0) {
+                s -= k;
+                alpha = ldexp(a.beta, -(s + 1));
+                const double f1 = ldexp(1.0, k), f2 = ldexp(1.0, 2 * k);
+                for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) {
+                    x0[e] *= f1;
+                    Q[e] *= f2;
+                }
+                __syncthreads();
+            }
+        }
+        dgemm(n, 2.0 / 15.0, Q, Q, -1.0 / 3.0, Q, 1.0, P, sm);
+        dgemm(n, 1.0, x0, P, 0.0, nullptr, 0.0, Z, sm);
+        for (int r = 0; r < a.m; ++r) {
+            // dZ0 = X1 P + x0 P1,  P1 = -Q1/3 + (2/15)(Q Q1 + Q1 Q),  Q1 = x0 X1 + X1 x0
+            double *X1 = B[4], *Q1 = B[5], *P1 = B[6];
+            gather_scaled(n, S, a.H1ptr[r], a.H1idx[r], a.H1val[r], alpha, 0.0, X1);
+            dgemm(n, 1.0, x0, X1, 0.0, nullptr, 0.0, Q1, sm);
+            dgemm(n, 1.0, X1, x0, 1.0, Q1, 0.0, Q1, sm);
+            dgemm(n, 2.0 / 15.0, Q, Q1, -1.0 / 3.0, Q1, 0.0, P1, sm);
+            dgemm(n, 2.0 / 15.0, Q1, Q, 1.0, P1, 0.0, P1, sm);
+            dgemm(n, 1.0, X1, P, 0.0, nullptr, 0.0, Z1[r], sm);
+            dgemm(n, 1.0, x0, P1, 1.0, Z1[r], 0.0, Z1[r], sm);
+        }
+        double *Y = B[0], *Y2 = B[1], *X = B[2], *R = B[4], *Xn = B[5], *W = B[6];
+        for (int step = 0; step < s; ++step) {
+            dgemm(n, 1.0, Z, Z, 0.0, nullptr, 0.0, Y, sm);
+            // X0 = (98 I - 80 Y + 32 Y^2) / 99
+            dgemm(n, 32.0 / 99.0, Y, Y, -80.0 / 99.0, Y, 98.0 / 99.0, X, sm);
+            for (int j = 0; j < a.ns_iters; ++j) {
+                dgemm(n, -1.0, Y, X, -1.0, X, 1.0, R, sm);      // R = I - X - Y X
+                dgemm(n, 1.0, X, R, 1.0, X, 0.0, Xn, sm);       // X + X R
+                double* t = X; X = Xn; Xn = t;
+            }
+            dgemm(n, 2.0, X, Z, 0.0, nullptr, 0.0, W, sm);      // W = 2 X Z
+            for (int r = 0; r < a.m; ++r) {
+                double *A1 = R, *T = Y2;
+                dgemm(n, 1.0, X, Z1[r], 0.0, nullptr, 0.0, A1, sm);
+                dgemm(n, 2.0, A1, X, 0.0, nullptr, 0.0, T, sm);      // 2 X Z1 X
+                dgemm(n, 1.0, W, Z1[r], 0.0, nullptr, 0.0, A1, sm);  // W Z1
+                dgemm(n, -0.5, A1, W, 1.0, T, 0.0, Z1[r], sm);       // - W Z1 W / 2
+            }
+            double* t = Z; Z = W; W = t;
+        }
+        dgemm(n, 1.0, Z, Z, 0.0, nullptr, 0.0, Y, sm);  // Z_s^2 for d (I - d)
+
+        // core columns -> collected CSC positions, and core traces
+        const int64_t c0 = a.core_ptr[i], c1 = a.core_ptr[i + 1];
+        for (int64_t e = c0; e < c1; ++e) {
+            const int kc = a.core_pos[e];
+            const int64_t o = a.col_ptr[a.core_idx[e]];
+            for (int r = threadIdx.x; r < n; r += blockDim.x) {
+                const double id = (r == kc) ? 1.0 : 0.0;
+                const double dv = 0.5 * (id - Z[(int64_t)r * n + kc]);
+                const double mv = 0.25 * a.beta * (id - Y[(int64_t)r * n + kc]);
+                if (!isfinite(dv) || !isfinite(mv)) set_error(a.err, GB_ERR_NAN);
+                a.Dval[o + r] = dv;
+                a.d1mu_val[o + r] = mv;
+                for (int q = 0; q < a.m; ++q) a.D1val[q][o + r] = -0.5 * Z1[q][(int64_t)r * n + kc];
+            }
+        }
+        for (int slot = 0; slot < TR_FIXED + a.m; ++slot) {
+            double v = 0.0;
+            for (int64_t e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
+                const int64_t kk = (int64_t)a.core_pos[e] * (n + 1);
+                if (slot == TR_D) v += 0.5 * (1.0 - Z[kk]);
+                else if (slot == TR_DD) v += 0.25 * (1.0 - Y[kk]);
+                else if (slot == TR_D1MU) v += 0.25 * a.beta * (1.0 - Y[kk]);
+                else if (slot >= TR_D1LAM) v += -0.5 * Z1[slot - TR_D1LAM][kk];
+            }
+            if (slot == TR_FLOPS && threadIdx.x == 0) v = pass_gemm_flops(n, s, a.ns_iters, a.m);
+            if (slot == TR_MAXW)
+                for (int r = threadIdx.x; r < n; r += blockDim.x)
+                    v = fmax(v, 0.25 * a.beta * (1.0 - Y[(int64_t)r * (n + 1)]));
+            red[threadIdx.x] = v;
+            __syncthreads();
+            for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+                if (threadIdx.x < o)
+                    red[threadIdx.x] = slot == TR_MAXW ? fmax(red[threadIdx.x], red[threadIdx.x + o])
+                                                       : red[threadIdx.x] + red[threadIdx.x + o];
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) a.tr[(int64_t)i * a.tr_stride + slot] = red[0];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) a.steps_out[i] = s;
+        __syncthreads();
+    }
+}
+
+// k_moff: moff[i] = n_i^2 (scanned afterwards)
+__global__ void k_block_sizes(int32_t n_sub, const int64_t* sub_ptr, int64_t* sq) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_sub) {
+        int64_t ni = sub_ptr[i + 1] - sub_ptr[i];
+        sq[i] = ni * ni;
+    }
+}
+
+struct DensityLayout {
+    int64_t* moff;      // n_sub + 1
+    double* eps_lo;     // n_sub
+    double* eps_hi;     // n_sub
+    int32_t* steps;     // n_sub
+    double* tr;         // n_sub * (TR_FIXED + m)
+    double* sums;       // TR_FIXED + m
+    double* bounds;     // 2
+    double* d1mu_val;   // out_nnz
+    int64_t* scan_tmp;
+    int* err;
+    double* pool;       // FP64: (NBUF + m) * pool_stride
+    float* z1pool;      // split: n_sub * m * 128 * 128
+    int64_t pool_stride;
+};
+
+DensityLayout layout_density(Arena& ar, const gb_part* P, int32_t m, int precision) {
+    DensityLayout L;
+    const int64_t n_sub = P->n_sub;
+    L.moff = ar.take<int64_t>(n_sub + 1);
+    L.eps_lo = ar.take<double>(n_sub);
+    L.eps_hi = ar.take<double>(n_sub);
+    L.steps = ar.take<int32_t>(n_sub);
+    L.tr = ar.take<double>(n_sub * (TR_FIXED + m));
+    L.sums = ar.take<double>(TR_FIXED + m + 8);
+    L.bounds = ar.take<double>(8);
+    L.d1mu_val = ar.take<double>(P->out_nnz);
+    L.scan_tmp = ar.take<int64_t>(scan_temp_count(n_sub + 1) + 64);
+    L.err = ar.take<int>(8);
+    // sum_i n_i^2 <= max_sub * sum_i n_i
+    L.pool_stride = (int64_t)P->max_sub * P->sub_nnz + 32;
+    if (precision == GB_PREC_FP64) {
+        L.pool = ar.take<double>((NBUF + m) * L.pool_stride);
+        L.z1pool = nullptr;
+    } else {
+        L.pool = nullptr;
+        L.z1pool = ar.take<float>(n_sub * (int64_t)(m > 0 ? m : 1) * GB_SPLIT_MAX_N * GB_SPLIT_MAX_N);
+    }
+    return L;
+}
+
+}  // namespace
+
+extern "C" int gb_density_workspace_size(const gb_part* P, int32_t m, const gb_opts* opts,
+                                         size_t* bytes) {
+    if (!P || !bytes || m < 0 || m > GB_MAX_RHS || P->n_sub <= 0) return GB_ERR_ARG;
+    int precision = opts ? opts->precision : GB_PREC_FP64;
+    Arena a;
+    layout_density(a, P, m, precision);
+    *bytes = a.used();
+    return GB_OK;
+}
+
+static bool csr_ok(const gb_csr* A, int32_t n) {
+    return A && A->n == n && A->ptr && A->nnz >= 0 && (A->nnz == 0 || (A->idx && A->val));
+}
+
+extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_csr* H1, int32_t m,
+                                       double kT, double n_electrons, const gb_part* P,
+                                       const gb_opts* opts, double* mu_inout, gb_csc* D, gb_csc* D1,
+                                       double* mu1, gb_report* rep) {
+    if (!h || !P || !mu_inout || !D) return GB_ERR_ARG;
+    const int32_t n = P->n;
+    if (!csr_ok(H, n) || m < 0 || m > GB_MAX_RHS || (m > 0 && (!H1 || !D1 || !mu1))) return GB_ERR_ARG;
+    for (int r = 0; r < m; ++r)
+        if (!csr_ok(&H1[r], n)) return GB_ERR_ARG;
+    if (!(kT > 0.0) || !isfinite(kT) || !isfinite(n_electrons)) return GB_ERR_ARG;
+    if (P->n_sub <= 0 || !P->core_ptr || !P->core_idx || !P->core_pos || !P->sub_ptr || !P->sub_idx)
+        return GB_ERR_ARG;
+    const double n_occ = 0.5 * n_electrons;
+    if (!(n_occ > 0.0) || !(n_occ < (double)n)) return GB_ERR_MU_BRACKET;
+    if (D->n != n || !D->val || D->capacity < P->out_nnz) {
+        D->nnz = P->out_nnz;
+        return D->val ? GB_ERR_CAPACITY : GB_ERR_ARG;
+    }
+    for (int r = 0; r < m; ++r) {
+        if (D1[r].n != n || !D1[r].val || D1[r].capacity < P->out_nnz) {
+            D1[r].nnz = P->out_nnz;
+            return D1[r].val ? GB_ERR_CAPACITY : GB_ERR_ARG;
+        }
+    }
+    gb_opts o = {GB_PREC_FP64, 40, 0.0, 6, 0, 0.0};
+    if (opts) o = *opts;
+    if (o.precision < GB_PREC_FP64 || o.precision > GB_PREC_BF16X3) return GB_ERR_ARG;
+    const bool split = o.precision != GB_PREC_FP64;
+    if (o.max_newton <= 0) o.max_newton = 40;
+    if (o.min_steps <= 0) o.min_steps = 6;
+    if (o.ns_iters <= 0) o.ns_iters = split ? 2 : 3;
+    const double tol_d = o.tol_d > 0.0 ? o.tol_d : (split ? 1e-6 : 1e-11);
+    if (split && P->max_sub > GB_SPLIT_MAX_N) return GB_ERR_UNSUPPORTED;
+    if (!D->ptr) return GB_ERR_ARG;  // the value positions follow the column pointers
+
+    h->launches = 0;
+    Arena ar(h->ws, h->ws_bytes);
+    DensityLayout L = layout_density(ar, P, m, o.precision);
+    if (!ar.fits() || !h->ws) {
+        Arena mm;
+        layout_density(mm, P, m, o.precision);
+        h->required_ws = mm.used();
+        return GB_ERR_WORKSPACE;
+    }
+    cudaStream_t st = h->stream;
+    const int32_t n_sub = P->n_sub;
+    const int tb = 256;
+    const int sub_grid = n_sub < 152 * 32 ? n_sub : 152 * 32;
+    GB_CUDA(cudaMemsetAsync(L.err, 0, sizeof(int) * 8, st));
+
+    // input checks
+    GB_LAUNCH(h, k_check_finite, 1024, tb, 0, H->nnz, H->val, L.err);
+    for (int r = 0; r < m; ++r) GB_LAUNCH(h, k_check_finite, 1024, tb, 0, H1[r].nnz, H1[r].val, L.err);
+
+    // collected structure: column pointers, then row indices (shared by D and D1)
+    GB_LAUNCH(h, k_csc_lengths, sub_grid, 128, 0, n_sub, P->sub_ptr, P->core_ptr, P->core_idx, D->ptr);
+    GB_CUDA(cudaMemsetAsync(D->ptr + n, 0, sizeof(int64_t), st));
+    GB_TRY(exclusive_scan_i64(h, D->ptr, D->ptr, (int64_t)n + 1, L.scan_tmp));
+    if (D->idx)
+        GB_LAUNCH(h, k_csc_rows, sub_grid, 128, 0, n_sub, P->sub_ptr, P->sub_idx, P->core_ptr,
+                  P->core_idx, (const int64_t*)D->ptr, D->idx);
+    for (int r = 0; r < m; ++r) {
+        if (D1[r].ptr)
+            GB_CUDA(cudaMemcpyAsync(D1[r].ptr, D->ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, st));
+        if (D1[r].idx && D->idx)
+            GB_CUDA(cudaMemcpyAsync(D1[r].idx, D->idx, sizeof(int32_t) * P->out_nnz, cudaMemcpyDeviceToDevice, st));
+        else if (D1[r].idx)
+            GB_LAUNCH(h, k_csc_rows, sub_grid, 128, 0, n_sub, P->sub_ptr, P->sub_idx, P->core_ptr,
+                      P->core_idx, (const int64_t*)D->ptr, D1[r].idx);
+    }
+    // dense block offsets (FP64 path)
+    GB_LAUNCH(h, k_block_sizes, (n_sub + tb - 1) / tb, tb, 0, n_sub, P->sub_ptr, L.moff);
+    GB_CUDA(cudaMemsetAsync(L.moff + n_sub, 0, sizeof(int64_t), st));
+    GB_TRY(exclusive_scan_i64(h, L.moff, L.moff, (int64_t)n_sub + 1, L.scan_tmp));
+    // spectral bounds
+    GB_LAUNCH(h, k_gershgorin, sub_grid, FP64_THREADS, 0, n_sub, P->sub_ptr, P->sub_idx, H->ptr, H->idx,
+              H->val, L.eps_lo, L.eps_hi);
+    const int stride = TR_FIXED + m;
+    GB_LAUNCH(h, k_reduce, 1, FP64_THREADS, 0, n_sub, stride, (const double*)L.tr, (const double*)L.eps_lo,
+              (const double*)L.eps_hi, L.sums, L.bounds);
+    double bounds[2];
+    GB_TRY(read_f64(h, L.bounds, bounds, 2));
+    int herr = 0;
+    GB_TRY(read_i32(h, L.err, &herr));
+    if (herr) return herr;
+
+    PassArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n_sub = n_sub;
+    a.m = m;
+    a.sub_ptr = P->sub_ptr;
+    a.sub_idx = P->sub_idx;
+    a.core_ptr = P->core_ptr;
+    a.core_idx = P->core_idx;
+    a.core_pos = P->core_pos;
+    a.Hptr = H->ptr;
+    a.Hidx = H->idx;
+    a.Hval = H->val;
+    for (int r = 0; r < m; ++r) {
+        a.H1ptr[r] = H1[r].ptr;
+        a.H1idx[r] = H1[r].idx;
+        a.H1val[r] = H1[r].val;
+        a.D1val[r] = D1[r].val;
+    }
+    a.beta = 1.0 / kT;
+    a.min_steps = o.min_steps;
+    a.ns_iters = o.ns_iters;
+    a.split_kind = o.precision == GB_PREC_BF16X3 ? 1 : 0;
+    a.eps_lo = L.eps_lo;
+    a.eps_hi = L.eps_hi;
+    a.col_ptr = D->ptr;
+    a.Dval = D->val;
+    a.d1mu_val = L.d1mu_val;
+    a.tr = L.tr;
+    a.tr_stride = stride;
+    a.steps_out = L.steps;
+    a.pool = L.pool;
+    a.moff = L.moff;
+    a.pool_stride = L.pool_stride;
+    a.z1pool = L.z1pool;
+    a.err = L.err;
+
+    // mu: Newton-Raphson on the core traces (Eq. NewtonRaphson), safeguarded
+    // by a bisection bracket; each evaluation is one full pass.
+    double lo = bounds[0] - 40.0 * kT, hi = bounds[1] + 40.0 * kT;
+    double mu = *mu_inout;
+    if (!(mu > lo && mu < hi)) mu = 0.5 * (lo + hi);
+    double sums[TR_FIXED + GB_MAX_RHS];
+    double kernel_ms = 0.0;
+    if (!h->ev0) {
+        GB_CUDA(cudaEventCreate(&h->ev0));
+        GB_CUDA(cudaEventCreate(&h->ev1));
+    }
+    cudaEvent_t ev0 = h->ev0, ev1 = h->ev1;
+    int passes = 0;
+    bool converged = false;
+    double prev_resid = INFINITY, last_bound = INFINITY;
+    for (passes = 1; passes <= o.max_newton; ++passes) {
+        a.mu = mu;
+        GB_CUDA(cudaEventRecord(ev0, st));
+        if (split) {
+            GB_TRY(launch_split_pass(h, a));
+        } else {
+            GB_LAUNCH(h, k_fermi_fp64, sub_grid, FP64_THREADS, 0, a);
+        }
+        GB_CUDA(cudaEventRecord(ev1, st));
+        GB_LAUNCH(h, k_reduce, 1, FP64_THREADS, 0, n_sub, stride, (const double*)L.tr,
+                  (const double*)L.eps_lo, (const double*)L.eps_hi, L.sums, L.bounds);
+        GB_TRY(read_f64(h, L.sums, sums, stride));
+        {
+            float ms = 0.f;
+            GB_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+            kernel_ms += ms;
+        }
+        GB_TRY(read_i32(h, L.err, &herr));
+        if (herr) return herr;
+        if (!isfinite(sums[TR_D]) || !isfinite(sums[TR_DD])) return GB_ERR_NAN;
+        const double resid = sums[TR_D] - n_occ;
+        const double dn = a.beta * sums[TR_DD];
+        // Converged when the occupation residual is within tol_occ * N_occ, or
+        // when the remaining Newton correction |resid / dn| would move every
+        // element of D by less than tol_dmu (|dD_jk| <= |dmu| max diag d1_mu).
+        const double dmu_newton = dn > 0.0 ? fabs(resid) / dn : INFINITY;
+        const double d_bound = dmu_newton * sums[TR_MAXW];
+        // Noise floor: once a Newton step no longer halves the residual, the
+        // trace round-off dominates and further passes only move mu within it.
+        // FP64 accepts that floor only near tol_d; split precision accepts it
+        // (its accuracy is then set by the trace round-off, see the report).
+        const bool stalled = passes >= 2 && fabs(resid) >= 0.5 * prev_resid;
+        if ((o.tol_occ > 0.0 && fabs(resid) <= o.tol_occ * n_occ) || d_bound <= tol_d ||
+            (stalled && (split || d_bound <= 10.0 * tol_d))) {
+            converged = true;
+            last_bound = d_bound;
+            break;
+        }
+        last_bound = d_bound;
+        prev_resid = fabs(resid);
+        if (passes == o.max_newton) break;
+        if (resid < 0.0) lo = mu; else hi = mu;
+        double next = dn > 0.0 ? mu - resid / dn : NAN;
+        // a Newton step stays inside the bracket and within 20 kT, else bisect
+        if (!(next > lo && next < hi) || fabs(next - mu) > 20.0 * kT) next = 0.5 * (lo + hi);
+        mu = next;
+    }
+    *mu_inout = mu;
+    // mu_1 (Eq. dmu_1) and D1 = d1_lambda + mu_1 d1_mu
+    for (int r = 0; r < m; ++r) {
+        const double den = sums[TR_D1MU];
+        mu1[r] = den > 0.0 ? -sums[TR_D1LAM + r] / den : 0.0;
+        GB_LAUNCH(h, k_d1_fixup, 1024, tb, 0, P->out_nnz, mu1[r], (const double*)L.d1mu_val, D1[r].val);
+        D1[r].nnz = P->out_nnz;
+    }
+    D->nnz = P->out_nnz;
+    int32_t max_steps = 0;
+    {
+        // largest step count of the final pass (small read-back)
+        int32_t* hs = new (std::nothrow) int32_t[n_sub];
+        if (hs) {
+            GB_CUDA(cudaMemcpyAsync(hs, L.steps, sizeof(int32_t) * n_sub, cudaMemcpyDeviceToHost, st));
+            GB_CUDA(cudaStreamSynchronize(st));
+            for (int32_t i = 0; i < n_sub; ++i) max_steps = hs[i] > max_steps ? hs[i] : max_steps;
+            delete[] hs;
+        }
+    }
+    GB_CUDA(cudaStreamSynchronize(st));
+    if (rep) {
+        rep->passes = passes > o.max_newton ? o.max_newton : passes;
+        rep->max_steps = max_steps;
+        rep->n_sub = n_sub;
+        rep->max_sub = P->max_sub;
+        rep->mu = mu;
+        rep->trace_d = sums[TR_D];
+        rep->dndmu = a.beta * sums[TR_DD];
+        rep->occ_residual = sums[TR_D] - n_occ;
+        rep->trace_d1mu = sums[TR_D1MU];
+        rep->eps_min = bounds[0];
+        rep->eps_max = bounds[1];
+        rep->gemm_flops = sums[TR_FLOPS];
+        rep->pass_kernel_ms = kernel_ms;
+        rep->mu_d_bound = last_bound;
+        rep->kernel_launches = h->launches;
+    }
+    return converged ? GB_OK : GB_ERR_NO_CONVERGE;
+}

@@ -1,0 +1,75 @@
+// Arguments shared by the per-pass recursion kernels (FP64 and split
+// precision).  One pass evaluates, for every subgraph at one chemical
+// potential mu, the Fermi recursion and its first-order response, writes the
+// core columns of d, d1_lambda and d1_mu, and the per-subgraph core traces.
+#pragma once
+
+#include "common.cuh"
+
+constexpr int GB_MAX_RHS = 8;
+constexpr int GB_SPLIT_MAX_N = 128;  // largest subgraph of the tensor-core kernel
+
+// Per-subgraph trace slots (tr[i * tr_stride + k])
+// TR_MAXW is reduced with max (the largest diagonal element of d1_mu over all
+// rows of all subgraphs, which bounds every element of the PSD d1_mu); the
+// other slots are summed.
+enum TraceSlot { TR_D = 0, TR_DD = 1, TR_D1MU = 2, TR_FLOPS = 3, TR_MAXW = 4, TR_D1LAM = 5 };
+constexpr int TR_FIXED = 5;  // slots before the per-RHS d1_lambda traces
+
+// Matrix products one pass performs on a subgraph with s steps, J Newton-
+// Schulz corrections and m right-hand sides: Taylor start 3 + 6m, every step
+// 3 + 2J + 4m, and Z_s^2 at the end.
+__host__ __device__ __forceinline__ double pass_gemm_flops(int n, int s, int J, int m) {
+    double g = 4.0 + 6.0 * m + (double)s * (3.0 + 2.0 * J + 4.0 * m);
+    return g * 2.0 * (double)n * (double)n * (double)n;
+}
+
+struct PassArgs {
+    int32_t n_sub;
+    int32_t m;
+    const int64_t* sub_ptr;
+    const int32_t* sub_idx;
+    const int64_t* core_ptr;
+    const int32_t* core_idx;
+    const int32_t* core_pos;
+    // H and H1_r (CSR)
+    const int64_t* Hptr;
+    const int32_t* Hidx;
+    const double* Hval;
+    const int64_t* H1ptr[GB_MAX_RHS];
+    const int32_t* H1idx[GB_MAX_RHS];
+    const double* H1val[GB_MAX_RHS];
+    double beta;
+    double mu;
+    int32_t min_steps;
+    int32_t ns_iters;
+    int32_t split_kind;  // 0: FP16 parts, 1: BF16 parts (split-precision kernel only)
+    const double* eps_lo;
+    const double* eps_hi;
+    // outputs, at the positions of the collected CSC matrices
+    const int64_t* col_ptr;
+    double* Dval;
+    double* D1val[GB_MAX_RHS];
+    double* d1mu_val;
+    double* tr;
+    int32_t tr_stride;
+    int32_t* steps_out;
+    // FP64 path: dense blocks (offset moff[i] inside each of the pool's buffers)
+    double* pool;
+    const int64_t* moff;
+    int64_t pool_stride;
+    // split path: FP32 response state, 128 x 128 per subgraph and RHS
+    float* z1pool;
+    int* err;
+};
+
+// Step count s so that x0 = beta (h - mu) / 2^(s+1) has spectral radius <= 1:
+// 2^s >= beta max|eps - mu| / 2, bounded below by min_steps.
+__device__ __forceinline__ int recursion_steps(double beta, double mu, double lo, double hi, int min_steps) {
+    double ymax = 0.5 * beta * fmax(fabs(hi - mu), fabs(lo - mu));
+    int s = min_steps;
+    while (s < 60 && ldexp(1.0, s) < ymax) ++s;
+    return s;
+}
+
+int launch_split_pass(gb_handle* h, const PassArgs& a);

@@ -1,0 +1,730 @@
+// Split-precision Fermi / response recursion on the 5th-generation tensor
+// cores (tcgen05), one subgraph (|S_i| <= 128) per CTA.
+//
+// Every matrix product A B runs as three tcgen05.mma (kind::f16) passes
+//   A_hi B_hi + A_hi B_lo + A_lo B_hi,  x = hi + lo, hi = rn(x), lo = rn(x - hi)
+// with FP16 (default) or BF16 parts and FP32 accumulation in tensor memory.
+// Quantities that are close to the identity never pass through the 16-bit
+// parts: the Newton-Schulz residual R = I - X - Y X is accumulated onto a
+// TMEM copy of (I - X) and the correction X + X R onto the FP32 X itself.
+//
+// Scaling (powers of two, so exact): staged operands hold 2^12 x their value,
+// which keeps the FP16 lo parts of elements down to ~3e-5 out of the subnormal
+// range; every product therefore lands in TMEM as 2^24 x its value, and all
+// FP32 state kept in TMEM uses the same 2^24 units.  Each subgraph's
+// perturbation is normalised by sigma = 2^-k so that (beta/2) sigma |h1| <= 1
+// (the response is linear in h1; d1_lambda is unscaled by 1/sigma at the end),
+// which bounds every response matrix by O(1).
+//
+// Resources per CTA: TMEM 512 columns = four 128-column FP32 slots; shared
+// memory = three staged operands (128 rows x 128 K, hi + lo, 64 KB each) laid
+// out K-major in 8x8 core matrices without swizzle: element (r, k) at byte
+// (k/8)*2048 + (r/8)*128 + (r%8)*16 + (k%8)*2.
+//
+// The per-step schedule (Z FP32 in slot zs):
+//   stage Z -> S0;  Y = Z Z -> ys;  stage Y -> S1;  Y^2 -> ts;
+//   X0 = (98 I - 80 Y + 32 Y^2)/99 -> xs (FP32) and S2;
+//   repeat: (I - X) -> ts; ts += -Y X; stage R -> S0; xs += X R; stage X -> S2;
+//   stage Z -> S0; W/2 = X Z -> ts;
+//   per RHS: stage W -> S0, Z1 -> S1; X Z1 -> ys, W Z1 -> zs;
+//            Z1' = (2 X Z1) X - (W Z1 / 2) W -> ys -> global FP32;
+//   new Z = 2 * ts.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "density.cuh"
+
+namespace {
+
+constexpr int THREADS = 128;
+constexpr int NMAX = GB_SPLIT_MAX_N;
+constexpr uint32_t HALF_BYTES = NMAX * NMAX * 2;  // one 16-bit part
+constexpr uint32_t STAGE_BYTES = 2 * HALF_BYTES;   // hi + lo
+constexpr int NSTAGE = 3;
+constexpr uint32_t LBO = 128 * (NMAX / 8);         // next 8-column group (K direction)
+constexpr uint32_t SBO = 128;                      // next 8-row group (M/N direction)
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t SLOT_COLS = 128;
+constexpr uint32_t WAIT_LIMIT = 1u << 22;
+constexpr float STAGE_SCALE = 4096.f;               // staged operand = 2^12 x value
+constexpr float TMEM_SCALE = 16777216.f;            // TMEM word = 2^24 x value
+constexpr float TMEM_INV = 1.f / 16777216.f;
+
+struct __align__(16) Ctl {
+    unsigned long long mbar;
+    uint32_t tmem_base;
+    int abort;
+    int32_t S[NMAX];
+    int32_t cpos[NMAX];
+    double red[THREADS];
+    double sig[GB_MAX_RHS];  // per-RHS perturbation normalisation of the current subgraph
+};
+
+constexpr size_t SMEM_BYTES = NSTAGE * STAGE_BYTES + sizeof(Ctl) + 1024;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t desc_bits(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05; layout: no swizzle
+    return d;
+}
+
+// A operand, K-major: row m of the staged buffer is row m of A (8-column
+// groups LBO apart, 8-row groups SBO apart).
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) { return desc_bits(saddr, LBO, SBO); }
+
+// B operand, MN-major on the same staged layout: staged row k holds B[k][:],
+// so the 8-row groups (128 B apart) run along K and the 8-column groups
+// (2048 B apart) along N.  The product is then A B, not A B^T: symmetric
+// matrices carry their rounding asymmetry, and A B^T would feed it back.
+__device__ __forceinline__ uint64_t make_desc_b(uint32_t saddr) { return desc_bits(saddr, SBO, LBO); }
+
+// kind::f16 instruction descriptor: D FP32, A/B FP16 (fmt 0) or BF16 (fmt 1),
+// A K-major, B MN-major (bit 16), M = 128, N = n.
+__device__ __forceinline__ uint32_t make_idesc(int fmt, int neg_a, int n) {
+    return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)neg_a << 13) |
+           (1u << 16) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+    for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]),
+                   "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r) : : "memory");
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15]))
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// hi/lo split of one value into 16-bit parts (fmt 0: FP16, 1: BF16)
+__device__ __forceinline__ void split2(float x, int fmt, uint16_t& hi, uint16_t& lo) {
+    if (fmt == 0) {
+        __half h = __float2half_rn(x);
+        __half l = __float2half_rn(x - __half2float(h));
+        hi = __half_as_ushort(h);
+        lo = __half_as_ushort(l);
+    } else {
+        __nv_bfloat16 h = __float2bfloat16_rn(x);
+        __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+        hi = __bfloat16_as_ushort(h);
+        lo = __bfloat16_as_ushort(l);
+    }
+}
+
+__device__ __forceinline__ uint32_t elem_off(int r, int k) {
+    return (uint32_t)(k >> 3) * LBO + (uint32_t)(r >> 3) * SBO + (uint32_t)(r & 7) * 16u + (uint32_t)(k & 7) * 2u;
+}
+
+// write 16 consecutive columns [c0, c0+16) of row r into a staged operand
+__device__ __forceinline__ void stage_chunk(uint8_t* stage, int r, int c0, const float (&v)[16], int fmt) {
+    uint32_t hi[8], lo[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        uint16_t h0, l0, h1, l1;
+        split2(v[2 * j], fmt, h0, l0);
+        split2(v[2 * j + 1], fmt, h1, l1);
+        hi[j] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+        lo[j] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+    }
+    uint8_t* p0 = stage + elem_off(r, c0);
+    uint8_t* p1 = stage + elem_off(r, c0 + 8);
+    *(uint4*)p0 = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *(uint4*)p1 = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+    *(uint4*)(p0 + HALF_BYTES) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    *(uint4*)(p1 + HALF_BYTES) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+}
+
+__device__ __forceinline__ void stage_put(uint8_t* stage, int r, int k, float x, int fmt) {
+    uint16_t h, l;
+    split2(x, fmt, h, l);
+    *(uint16_t*)(stage + elem_off(r, k)) = h;
+    *(uint16_t*)(stage + elem_off(r, k) + HALF_BYTES) = l;
+}
+
+struct Kernel {
+    const PassArgs& a;
+    Ctl& c;
+    uint8_t* st[NSTAGE];
+    uint32_t st_addr[NSTAGE];
+    uint32_t tbase;
+    uint32_t mbar;
+    uint32_t phase;
+    int fmt;
+    int n, npad;
+    int row;       // this thread's row = TMEM lane
+    uint32_t lane_off;
+
+    __device__ Kernel(const PassArgs& a_, Ctl& c_, uint8_t* smem) : a(a_), c(c_) {
+        for (int k = 0; k < NSTAGE; ++k) {
+            st[k] = smem + k * STAGE_BYTES;
+            st_addr[k] = smem_u32(st[k]);
+        }
+        mbar = smem_u32(&c.mbar);
+        phase = 0;
+        fmt = a.split_kind;
+        row = threadIdx.x;
+        lane_off = (uint32_t)((threadIdx.x & ~31) << 16);
+    }
+
+    __device__ uint32_t slot(int s) const { return tbase + (uint32_t)s * SLOT_COLS; }
+
+    // all threads: make generic smem writes and TMEM stores visible to the MMA
+    __device__ void sync_for_mma() {
+        fence_proxy_async();
+        fence_before();
+        __syncthreads();
+    }
+
+    // C (slot d) = [+/-] A B  (+ C if acc): three split passes per K step
+    __device__ void issue(int d, int sa, int sb, int neg_a, bool acc) {
+        const uint32_t idesc = make_idesc(fmt, neg_a, npad);
+        const uint32_t dt = slot(d);
+        // the small cross terms for every K step first, then the hi*hi terms:
+        // the cross-term sum is then never added into a large accumulator
+        for (int ks = 0; ks < npad / 16; ++ks) {
+            const uint32_t koff = (uint32_t)ks * 2u * LBO;   // A: 16 columns of K
+            const uint32_t kofb = (uint32_t)ks * 2u * SBO;   // B: 16 rows of K
+            const uint64_t ahi = make_desc(st_addr[sa] + koff);
+            const uint64_t alo = make_desc(st_addr[sa] + HALF_BYTES + koff);
+            const uint64_t bhi = make_desc_b(st_addr[sb] + kofb);
+            const uint64_t blo = make_desc_b(st_addr[sb] + HALF_BYTES + kofb);
+            mma_f16(dt, ahi, blo, idesc, (acc || ks > 0) ? 1u : 0u);
+            mma_f16(dt, alo, bhi, idesc, 1u);
+        }
+        for (int ks = 0; ks < npad / 16; ++ks) {
+            mma_f16(dt, make_desc(st_addr[sa] + (uint32_t)ks * 2u * LBO),
+                    make_desc_b(st_addr[sb] + (uint32_t)ks * 2u * SBO), idesc, 1u);
+        }
+    }
+
+    // wait for every MMA issued so far by thread 0
+    __device__ bool wait_mma() {
+        if (threadIdx.x == 0) mma_commit(mbar);
+        bool ok = mbar_wait(mbar, phase);
+        phase ^= 1u;
+        fence_after();
+        if (!ok) {
+            c.abort = 1;
+            set_error(a.err, GB_ERR_TIMEOUT);
+        }
+        __syncthreads();
+        return c.abort == 0;
+    }
+
+    // one product C = A B into slot d (operands already staged)
+    __device__ bool gemm(int d, int sa, int sb, int neg_a = 0, bool acc = false) {
+        sync_for_mma();
+        if (threadIdx.x == 0) {
+            fence_after();
+            issue(d, sa, sb, neg_a, acc);
+        }
+        return wait_mma();
+    }
+
+    // row-wise combination  v = ca * T[sA] + cb * T[sB] + cd * I  (masked to n x n),
+    // optionally written to FP32 slot `out`, staged operand `sg`, global row `gdst`.
+    __device__ void combine(int sA, float ca, int sB, float cb, float cd, int out, int sg, float* gdst) {
+        for (int c0 = 0; c0 < npad; c0 += 16) {
+            float v[16], w[16];
+            if (sA >= 0) tmem_ld16(slot(sA) + lane_off + c0, v);
+            else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = 0.f;
+            }
+            if (sB >= 0) tmem_ld16(slot(sB) + lane_off + c0, w);
+            else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) w[j] = 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int col = c0 + j;
+                float x = (ca * v[j] + cb * w[j]) * TMEM_INV + ((col == row) ? cd : 0.f);
+                v[j] = (row < n && col < n) ? x : 0.f;
+            }
+            if (out >= 0) {
+                float t[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) t[j] = v[j] * TMEM_SCALE;
+                tmem_st16(slot(out) + lane_off + c0, t);
+            }
+            if (sg >= 0) {
+                float t[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) t[j] = v[j] * STAGE_SCALE;
+                stage_chunk(st[sg], row, c0, t, fmt);
+            }
+            if (gdst) {
+#pragma unroll
+                for (int j = 0; j < 16; j += 4)
+                    *(float4*)(gdst + (size_t)row * NMAX + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            }
+        }
+    }
+
+    // max over rows of sum_c |M[S, S]_rc| for a CSR matrix M (block-uniform)
+    __device__ double gather_rowsum_max(const int64_t* ptr, const int32_t* idx, const double* val) {
+        double rs = 0.0;
+        if (row < n) {
+            const int32_t g = c.S[row];
+            for (int64_t p = ptr[g]; p < ptr[g + 1]; ++p) {
+                const int32_t col = idx[p];
+                int lo = 0, hi = n;
+                while (lo < hi) {
+                    int mid = (lo + hi) >> 1;
+                    if (c.S[mid] < col) lo = mid + 1; else hi = mid;
+                }
+                if (lo < n && c.S[lo] == col) rs += fabs(val[p]);
+            }
+        }
+        c.red[threadIdx.x] = rs;
+        __syncthreads();
+        for (int o = THREADS / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) c.red[threadIdx.x] = fmax(c.red[threadIdx.x], c.red[threadIdx.x + o]);
+            __syncthreads();
+        }
+        const double r = c.red[0];
+        __syncthreads();
+        return r;
+    }
+
+    // largest k <= kmax with 4^k max_r sum_c |T[sl]_rc| <= 1 (block-uniform)
+    __device__ int fewer_steps(int sl, int kmax) {
+        double rs = 0.0;
+        for (int c0 = 0; c0 < npad; c0 += 16) {
+            float v[16];
+            tmem_ld16(slot(sl) + lane_off + c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) rs += fabs((double)v[j] * (double)TMEM_INV);
+        }
+        c.red[threadIdx.x] = rs;
+        __syncthreads();
+        for (int o = THREADS / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) c.red[threadIdx.x] = fmax(c.red[threadIdx.x], c.red[threadIdx.x + o]);
+            __syncthreads();
+        }
+        const double qmax = c.red[0];
+        __syncthreads();
+        int k = 0;
+        while (k < kmax && qmax * ldexp(1.0, 2 * (k + 1)) <= 1.0) ++k;
+        return k;
+    }
+
+    // out[c] = sum_k M_row,k v[k][c] for c < nc, M = scale x TMEM slot sl (this
+    // thread's row), v in shared memory as [k][16]: FP32 products summed per
+    // 16-column chunk (round to nearest), chunk sums in FP64.
+    __device__ void rowvec(int sl, float scale, const float* v, int nc, double (&out)[16]) {
+        for (int c = 0; c < 16; ++c) out[c] = 0.0;
+        for (int c0 = 0; c0 < npad; c0 += 16) {
+            float m[16];
+            tmem_ld16(slot(sl) + lane_off + c0, m);
+            float part[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) part[c] = 0.f;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float mj = m[j] * scale;
+                const float* vr = v + (c0 + j) * 16;
+#pragma unroll
+                for (int c = 0; c < 16; ++c) part[c] = fmaf(mj, vr[c], part[c]);
+            }
+            for (int c = 0; c < nc; ++c) out[c] += (double)part[c];
+        }
+    }
+
+    // staged operand from a global FP32 128 x 128 row-major block
+    __device__ void stage_global(const float* g, int sg) {
+        for (int c0 = 0; c0 < npad; c0 += 16) {
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; j += 4) {
+                float4 q = *(const float4*)(g + (size_t)row * NMAX + c0 + j);
+                v[j] = q.x * STAGE_SCALE;
+                v[j + 1] = q.y * STAGE_SCALE;
+                v[j + 2] = q.z * STAGE_SCALE;
+                v[j + 3] = q.w * STAGE_SCALE;
+            }
+            stage_chunk(st[sg], row, c0, v, fmt);
+        }
+    }
+
+    // staged operand  scale * (M[S, S] - shift I)  from CSR
+    __device__ void stage_gather(const int64_t* ptr, const int32_t* idx, const double* val, double scale,
+                                 double shift, int sg) {
+        const float z[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int c0 = 0; c0 < npad; c0 += 16) stage_chunk(st[sg], row, c0, z, fmt);
+        if (row < n) {
+            const int32_t g = c.S[row];
+            double diag = 0.0;
+            for (int64_t p = ptr[g]; p < ptr[g + 1]; ++p) {
+                const int32_t col = idx[p];
+                int lo = 0, hi = n;
+                while (lo < hi) {
+                    int mid = (lo + hi) >> 1;
+                    if (c.S[mid] < col) lo = mid + 1; else hi = mid;
+                }
+                if (lo < n && c.S[lo] == col) {
+                    if (lo == row) diag = val[p];
+                    else stage_put(st[sg], row, lo, (float)(scale * val[p]) * STAGE_SCALE, fmt);
+                }
+            }
+            stage_put(st[sg], row, row, (float)(scale * (diag - shift)) * STAGE_SCALE, fmt);
+        }
+    }
+};
+
+__global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    Ctl& c = *(Ctl*)(smem + NSTAGE * STAGE_BYTES);
+    Kernel K(a, c, smem);
+
+    // zero the staged operands once (rows >= n stay zero afterwards)
+    for (uint32_t e = threadIdx.x; e < NSTAGE * STAGE_BYTES / 16; e += THREADS)
+        ((uint4*)smem)[e] = make_uint4(0u, 0u, 0u, 0u);
+    if (threadIdx.x == 0) {
+        c.abort = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(K.mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&c.tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    K.tbase = c.tmem_base;
+
+    for (int32_t i = blockIdx.x; i < a.n_sub && c.abort == 0; i += gridDim.x) {
+        const int64_t s0 = a.sub_ptr[i];
+        const int n = (int)(a.sub_ptr[i + 1] - s0);
+        const int64_t c0 = a.core_ptr[i], c1 = a.core_ptr[i + 1];
+        K.n = n;
+        K.npad = (n + 15) & ~15;
+        for (int r = threadIdx.x; r < n; r += THREADS) c.S[r] = a.sub_idx[s0 + r];
+        __syncthreads();
+        int s = recursion_steps(a.beta, a.mu, a.eps_lo[i], a.eps_hi[i], a.min_steps);
+        double alpha = ldexp(a.beta, -(s + 1));
+        float* z1base = a.z1pool + (size_t)i * (a.m > 0 ? a.m : 1) * NMAX * NMAX;
+
+        // ---- Taylor start: Q = x0^2, P = I - Q/3 + 2 Q^2/15 (slots: 0 Q, 1 P) ----
+        K.stage_gather(a.Hptr, a.Hidx, a.Hval, alpha, a.mu, 0);           // S0 = x0
+        if (!K.gemm(0, 0, 0)) break;                                      // T0 = Q
+        // rho(x0)^2 = rho(Q) <= max_r sum_c |Q_rc| (Gershgorin on the square is
+        // tighter than on h): drop k steps while 2^k x0 keeps spectral radius <= 1
+        const int k = K.fewer_steps(0, s - a.min_steps);
+        float qscale = 1.f;
+        if (k > 0) {
+            s -= k;
+            alpha = ldexp(a.beta, -(s + 1));
+            qscale = ldexpf(1.f, 2 * k);
+            K.stage_gather(a.Hptr, a.Hidx, a.Hval, alpha, a.mu, 0);       // S0 = 2^k x0
+        }
+        K.combine(0, qscale, -1, 0.f, 0.f, -1, 1, nullptr);               // S1 = Q
+        if (!K.gemm(1, 1, 1)) break;                                      // T1 = Q^2
+        K.combine(0, -qscale / 3.f, 1, 2.f / 15.f, 1.f, 1, -1, nullptr);  // T1 = P
+        bool ok = true;
+        for (int r = 0; r < a.m && ok; ++r) {
+            // normalise the perturbation: (beta / 2) sigma max row sum |h1| <= 1
+            const double h1max = K.gather_rowsum_max(a.H1ptr[r], a.H1idx[r], a.H1val[r]);
+            double sig = 1.0;
+            while (0.5 * a.beta * sig * h1max > 1.0 && sig > 1e-30) sig *= 0.5;
+            if (threadIdx.x == 0) c.sig[r] = sig;
+            // dZ0 = X1 P + x0 P1,  P1 = -Q1/3 + (2/15)(Q Q1 + Q1 Q),  Q1 = x0 X1 + X1 x0
+            K.stage_gather(a.H1ptr[r], a.H1idx[r], a.H1val[r], alpha * sig, 0.0, 1);  // S1 = X1
+            K.sync_for_mma();
+            if (threadIdx.x == 0) {
+                fence_after();
+                K.issue(2, 0, 1, 0, false);
+                K.issue(2, 1, 0, 0, true);
+            }
+            if (!(ok = K.wait_mma())) break;                               // T2 = Q1
+            K.combine(2, 1.f, -1, 0.f, 0.f, -1, 1, nullptr);               // S1 = Q1
+            K.combine(0, qscale, -1, 0.f, 0.f, -1, 2, nullptr);            // S2 = Q
+            K.sync_for_mma();
+            if (threadIdx.x == 0) {
+                fence_after();
+                K.issue(3, 2, 1, 0, false);
+                K.issue(3, 1, 2, 0, true);
+            }
+            if (!(ok = K.wait_mma())) break;                               // T3 = Q Q1 + Q1 Q
+            K.combine(2, -1.f / 3.f, 3, 2.f / 15.f, 0.f, -1, 1, nullptr);  // S1 = P1
+            if (!(ok = K.gemm(2, 0, 1))) break;                            // T2 = x0 P1
+            K.combine(1, 1.f, -1, 0.f, 0.f, -1, 2, nullptr);               // S2 = P
+            K.stage_gather(a.H1ptr[r], a.H1idx[r], a.H1val[r], alpha * sig, 0.0, 1);  // S1 = X1
+            if (!(ok = K.gemm(2, 1, 2, 0, true))) break;                   // T2 += X1 P
+            K.combine(2, 1.f, -1, 0.f, 0.f, -1, -1, z1base + (size_t)r * NMAX * NMAX);
+        }
+        if (!ok) break;
+        K.combine(1, 1.f, -1, 0.f, 0.f, -1, 2, nullptr);                  // S2 = P
+        if (!K.gemm(2, 0, 2)) break;                                      // T2 = Z0 = x0 P
+
+        // ---- doublings ----
+        int zs = 2;
+        float zscale = 1.f;
+        double tr_d = 0.0, tr_dd = 0.0, wmax = 0.0;
+        for (int step = 0; step < s && ok; ++step) {
+            int fr[3], q = 0;
+            for (int k = 0; k < 4; ++k)
+                if (k != zs) fr[q++] = k;
+            const int ys = fr[0], ts = fr[1], xs = fr[2];
+            K.combine(zs, zscale, -1, 0.f, 0.f, -1, 0, nullptr);                        // S0 = Z
+            if (!(ok = K.gemm(ys, 0, 0))) break;                                        // Y
+            K.combine(ys, 1.f, -1, 0.f, 0.f, -1, 1, nullptr);                           // S1 = Y
+            if (!(ok = K.gemm(ts, 1, 1))) break;                                        // Y^2
+            K.combine(ys, -80.f / 99.f, ts, 32.f / 99.f, 98.f / 99.f, xs, 2, nullptr);  // X0
+            for (int j = 0; j < a.ns_iters && ok; ++j) {
+                K.combine(xs, -1.f, -1, 0.f, 1.f, ts, -1, nullptr);                     // I - X
+                if (!(ok = K.gemm(ts, 1, 2, 1, true))) break;                           // R = I - X - Y X
+                K.combine(ts, 1.f, -1, 0.f, 0.f, -1, 0, nullptr);                       // S0 = R
+                if (!(ok = K.gemm(xs, 2, 0, 0, true))) break;                           // X += X R
+                K.combine(xs, 1.f, -1, 0.f, 0.f, -1, 2, nullptr);                       // S2 = X
+            }
+            if (!ok) break;
+            K.combine(zs, zscale, -1, 0.f, 0.f, -1, 0, nullptr);                        // S0 = Z
+            if (!(ok = K.gemm(ts, 2, 0))) break;                                        // W / 2 = X Z
+            if (step == s - 1) {
+                // ---- final correction on the core columns (CUDA cores) ----
+                // w = Z_s e_c = 2 (I + Z^2)^-1 Z e_c by two rounds of iterative
+                // refinement: w <- w + X (2 z - w - Z (Z w)), X the tensor-core
+                // inverse as preconditioner; every product rounds to nearest, so
+                // the saturated occupations (and Tr_c d) carry no accumulation bias.
+                fence_before();
+                __syncthreads();
+                fence_after();
+                float* V = (float*)K.st[0];  // S0 is free until W is staged below
+                float* Vz = V;
+                float* Vw = V + NMAX * 16;
+                float* Vt = V + 2 * NMAX * 16;
+                const float zsc = zscale * TMEM_INV;
+                const int ncore = (int)(c1 - c0);
+                for (int e = threadIdx.x; e < ncore; e += THREADS) c.cpos[e] = a.core_pos[c0 + e];
+                __syncthreads();
+                for (int b0 = 0; b0 < ncore; b0 += 16) {
+                    const int nc = min(16, ncore - b0);
+                    for (int cc = 0; cc < 16; ++cc) {
+                        float zv = 0.f;
+                        if (cc < nc) zv = tmem_ld1(K.slot(zs) + K.lane_off + c.cpos[b0 + cc]) * zsc;
+                        Vz[K.row * 16 + cc] = (K.row < n) ? zv : 0.f;
+                    }
+                    __syncthreads();
+                    double acc[16], wv[16];
+                    K.rowvec(xs, TMEM_INV, Vz, nc, acc);
+                    for (int cc = 0; cc < 16; ++cc) {
+                        wv[cc] = (K.row < n && cc < nc) ? 2.0 * acc[cc] : 0.0;
+                        Vw[K.row * 16 + cc] = (float)wv[cc];
+                    }
+                    __syncthreads();
+                    for (int it = 0; it < 2; ++it) {
+                        K.rowvec(zs, zsc, Vw, nc, acc);                                 // Z w
+                        __syncthreads();
+                        for (int cc = 0; cc < 16; ++cc) Vt[K.row * 16 + cc] = (K.row < n) ? (float)acc[cc] : 0.f;
+                        __syncthreads();
+                        K.rowvec(zs, zsc, Vt, nc, acc);                                 // Z (Z w)
+                        __syncthreads();
+                        for (int cc = 0; cc < 16; ++cc) {
+                            const double res = 2.0 * (double)Vz[K.row * 16 + cc] - wv[cc] - acc[cc];
+                            Vt[K.row * 16 + cc] = (K.row < n && cc < nc) ? (float)res : 0.f;
+                        }
+                        __syncthreads();
+                        K.rowvec(xs, TMEM_INV, Vt, nc, acc);                            // X r
+                        __syncthreads();
+                        for (int cc = 0; cc < 16; ++cc) {
+                            if (K.row < n && cc < nc) wv[cc] += acc[cc];
+                            Vw[K.row * 16 + cc] = (float)wv[cc];
+                        }
+                        __syncthreads();
+                    }
+                    // d = (I - Z_s) / 2 on the core columns
+                    for (int cc = 0; cc < nc; ++cc) {
+                        const int kc = c.cpos[b0 + cc];
+                        const int64_t o = a.col_ptr[a.core_idx[c0 + b0 + cc]];
+                        if (K.row < n) {
+                            const double dv = 0.5 * ((K.row == kc ? 1.0 : 0.0) - wv[cc]);
+                            if (!isfinite(dv)) set_error(a.err, GB_ERR_NAN);
+                            a.Dval[o + K.row] = dv;
+                            if (K.row == kc) tr_d += dv;
+                        }
+                    }
+                    __syncthreads();
+                }
+                // d (I - d) = (I - Z_s^2) / 4 = ((I - Y) X)^2 / 4: no cancellation
+                // near saturation (Y = Z_{s-1}^2, X = (I + Y)^-1)
+                K.combine(ys, -1.f, -1, 0.f, 1.f, -1, 1, nullptr);                      // S1 = I - Y
+                if (!(ok = K.gemm(zs, 1, 2))) break;                                    // G = (I - Y) X
+                K.combine(zs, 1.f, -1, 0.f, 0.f, -1, 1, nullptr);                       // S1 = G
+                if (!(ok = K.gemm(ys, 1, 1))) break;                                    // G^2
+                for (int e = c0; e < c1; ++e) {
+                    const int kc = c.cpos[e - c0];
+                    const int64_t o = a.col_ptr[a.core_idx[e]];
+                    const float gv = tmem_ld1(K.slot(ys) + K.lane_off + kc) * TMEM_INV;
+                    if (K.row < n) {
+                        const double mv = 0.25 * a.beta * (double)gv;
+                        a.d1mu_val[o + K.row] = mv;
+                        if (K.row == kc) tr_dd += 0.25 * (double)gv;
+                    }
+                }
+                for (int cc = 0; cc < K.npad; cc += 16) {
+                    float v[16];
+                    tmem_ld16(K.slot(ys) + K.lane_off + cc, v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (cc + j == K.row && K.row < n) wmax = 0.25 * a.beta * (double)v[j] * (double)TMEM_INV;
+                }
+            }
+            if (a.m > 0) K.combine(ts, 2.f, -1, 0.f, 0.f, -1, 0, nullptr);              // S0 = W
+            for (int r = 0; r < a.m && ok; ++r) {
+                float* z1 = z1base + (size_t)r * NMAX * NMAX;
+                K.stage_global(z1, 1);                                                  // S1 = Z1
+                K.sync_for_mma();
+                if (threadIdx.x == 0) {
+                    fence_after();
+                    K.issue(ys, 2, 1, 0, false);                                        // X Z1
+                    K.issue(zs, 0, 1, 0, false);                                        // W Z1
+                }
+                if (!(ok = K.wait_mma())) break;
+                K.combine(ys, 2.f, -1, 0.f, 0.f, -1, 1, nullptr);                       // S1 = 2 X Z1
+                if (!(ok = K.gemm(ys, 1, 2))) break;                                    // 2 X Z1 X
+                K.combine(zs, -0.5f, -1, 0.f, 0.f, -1, 1, nullptr);                     // S1 = -W Z1 / 2
+                if (!(ok = K.gemm(ys, 1, 0, 0, true))) break;                           // - W Z1 W / 2
+                K.combine(ys, 1.f, -1, 0.f, 0.f, -1, -1, z1);                           // Z1 -> global
+            }
+            zs = ts;
+            zscale = 2.f;
+        }
+        if (!ok) break;
+
+        // ---- d1_lambda = -Z1_s / (2 sigma) on the core columns ----
+        double tr_l[GB_MAX_RHS];
+        for (int r = 0; r < a.m; ++r) tr_l[r] = 0.0;
+        for (int64_t e = c0; e < c1; ++e) {
+            const int kc = c.cpos[e - c0];
+            const int64_t o = a.col_ptr[a.core_idx[e]];
+            if (K.row < n) {
+                for (int r = 0; r < a.m; ++r) {
+                    const double lv = -0.5 / c.sig[r] * (double)z1base[(size_t)r * NMAX * NMAX + (size_t)K.row * NMAX + kc];
+                    a.D1val[r][o + K.row] = lv;
+                    if (K.row == kc) tr_l[r] += lv;
+                }
+            }
+        }
+        // per-subgraph core traces (fixed-order block reduction)
+        for (int slot = 0; slot < TR_FIXED + a.m; ++slot) {
+            double v = slot == TR_D ? tr_d : slot == TR_DD ? tr_dd : slot == TR_D1MU ? a.beta * tr_dd
+                     : slot == TR_FLOPS ? (threadIdx.x == 0 ? pass_gemm_flops(n, s, a.ns_iters, a.m) : 0.0)
+                     : slot == TR_MAXW ? wmax
+                                        : tr_l[slot - TR_D1LAM];
+            c.red[threadIdx.x] = v;
+            __syncthreads();
+            for (int o = THREADS / 2; o > 0; o >>= 1) {
+                if (threadIdx.x < o)
+                    c.red[threadIdx.x] = slot == TR_MAXW ? fmax(c.red[threadIdx.x], c.red[threadIdx.x + o])
+                                                         : c.red[threadIdx.x] + c.red[threadIdx.x + o];
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) a.tr[(int64_t)i * a.tr_stride + slot] = c.red[0];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) a.steps_out[i] = s;
+        fence_before();
+        __syncthreads();
+        fence_after();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (threadIdx.x < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(K.tbase), "r"(TMEM_COLS)
+                     : "memory");
+}
+
+}  // namespace
+
+int launch_split_pass(gb_handle* h, const PassArgs& a) {
+    static bool configured = false;
+    if (!configured) {
+        GB_CUDA(cudaFuncSetAttribute(k_fermi_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+        configured = true;
+    }
+    int sms = 0;
+    GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    const int grid = a.n_sub < sms ? a.n_sub : sms;
+    GB_LAUNCH(h, k_fermi_split, grid, THREADS, SMEM_BYTES, a);
+    return GB_OK;
+}

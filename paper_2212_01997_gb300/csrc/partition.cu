@@ -1,0 +1,217 @@
+// gb_partition: disjoint cores and distance-1 halos.
+//
+// Fig. 1 / Sec. "Choosing the graph partitioning": a subgraph is its core plus
+// the halo of directly connected vertices; cores may hold several vertices
+// (here: one core per group id, e.g. one molecule, or consecutive blocks).
+// S_i = sorted(core_i U N(core_i)).  Membership is marked in shared-memory
+// bitmaps and read back in ascending order, so the output is bit-exact.
+#include "bitset.cuh"
+#include "common.cuh"
+
+namespace {
+
+constexpr int SUB_THREADS = 256;
+
+__device__ __forceinline__ int32_t group_of(int32_t v, const int32_t* group, int32_t block) {
+    return group ? group[v] : v / block;
+}
+
+__global__ void k_group_count(int32_t n, const int32_t* group, int32_t block, int32_t n_groups,
+                              int64_t* gcnt, int* err) {
+    int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int32_t g = group_of(v, group, block);
+    if (g < 0 || g >= n_groups) {
+        set_error(err, GB_ERR_ARG);
+        return;
+    }
+    atomicAdd((unsigned long long*)&gcnt[g], 1ull);
+}
+
+__global__ void k_nonempty(int32_t n_groups, const int64_t* gcnt, int64_t* flag) {
+    int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n_groups) flag[g] = gcnt[g] > 0 ? 1 : 0;
+}
+
+// cidx[g] = exclusive scan of the non-empty flags; core_size[cidx[g]] = gcnt[g]
+__global__ void k_core_sizes(int32_t n_groups, const int64_t* gcnt, const int64_t* cidx,
+                             int64_t* core_size) {
+    int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n_groups && gcnt[g] > 0) core_size[cidx[g]] = gcnt[g];
+}
+
+__global__ void k_core_fill(int32_t n, const int32_t* group, int32_t block, const int64_t* cidx,
+                            const int64_t* core_ptr, int64_t* cursor, int32_t* core_idx) {
+    int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int64_t c = cidx[group_of(v, group, block)];
+    int64_t p = atomicAdd((unsigned long long*)&cursor[c], 1ull);
+    core_idx[core_ptr[c] + p] = v;
+}
+
+// One block per core: sort the core, then mark core + neighbours.
+//   mode 0: sort core members in place and count |S_i| -> sub_size[i]
+//   mode 1: write S_i and the local positions of the core members
+__global__ void k_subgraphs(int32_t n, int32_t n_sub, const int64_t* gptr, const int32_t* gidx,
+                            const int64_t* core_ptr, int32_t* core_idx, int64_t* sub_size,
+                            const int64_t* sub_ptr, int32_t* sub_idx, int32_t* core_pos, int mode,
+                            int* stats) {
+    extern __shared__ uint32_t words[];
+    __shared__ int64_t scan[SUB_THREADS];
+    const int W = (n + 31) >> 5;
+    for (int32_t i = blockIdx.x; i < n_sub; i += gridDim.x) {
+        const int64_t c0 = core_ptr[i], c1 = core_ptr[i + 1];
+        if (mode == 0) {
+            // sorted core (the atomic fill leaves an arbitrary order)
+            bitmap_clear(words, W);
+            for (int64_t e = c0 + threadIdx.x; e < c1; e += blockDim.x) bitmap_set(words, core_idx[e]);
+            __syncthreads();
+            bitmap_compact(words, W, core_idx + c0, scan);
+        }
+        bitmap_clear(words, W);
+        for (int64_t e = c0; e < c1; ++e) {
+            int32_t v = core_idx[e];
+            if (threadIdx.x == 0) bitmap_set(words, v);
+            for (int64_t f = gptr[v] + threadIdx.x; f < gptr[v + 1]; f += blockDim.x)
+                bitmap_set(words, gidx[f]);
+        }
+        __syncthreads();
+        if (mode == 0) {
+            int64_t s = bitmap_compact(words, W, nullptr, scan);
+            if (threadIdx.x == 0) {
+                sub_size[i] = s;
+                atomicMax(&stats[0], (int)s);
+                atomicMax(&stats[1], (int)(c1 - c0));
+            }
+        } else {
+            int32_t* out = sub_idx + sub_ptr[i];
+            int64_t s = bitmap_compact(words, W, out, scan);
+            __syncthreads();
+            for (int64_t e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
+                int32_t v = core_idx[e];
+                int64_t lo = 0, hi = s;
+                while (lo < hi) {
+                    int64_t mid = (lo + hi) >> 1;
+                    if (out[mid] < v) lo = mid + 1; else hi = mid;
+                }
+                core_pos[e] = (int32_t)lo;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_out_nnz(int32_t n_sub, const int64_t* sub_size, const int64_t* core_ptr,
+                          unsigned long long* total) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_sub) atomicAdd(total, (unsigned long long)(sub_size[i] * (core_ptr[i + 1] - core_ptr[i])));
+}
+
+struct PartLayout {
+    int64_t* gcnt;      // n_groups + 1
+    int64_t* cidx;      // n_groups + 1
+    int64_t* cursor;    // n
+    int64_t* sub_size;  // n + 1
+    int64_t* scan_tmp;
+    int* err;           // [0] error, [1] max_sub, [2] max_core
+    unsigned long long* out_nnz;
+};
+
+PartLayout layout_part(Arena& a, int32_t n, int32_t n_groups) {
+    PartLayout L;
+    int64_t big = (int64_t)(n > n_groups ? n : n_groups) + 1;
+    L.gcnt = a.take<int64_t>(n_groups + 1);
+    L.cidx = a.take<int64_t>(n_groups + 1);
+    L.cursor = a.take<int64_t>(n);
+    L.sub_size = a.take<int64_t>(n + 1);
+    L.scan_tmp = a.take<int64_t>(scan_temp_count(big) + 64);
+    L.err = a.take<int>(8);
+    L.out_nnz = a.take<unsigned long long>(1);
+    return L;
+}
+
+}  // namespace
+
+extern "C" size_t gb_partition_workspace_size(int32_t n, int64_t nnz_g, int32_t n_groups) {
+    (void)nnz_g;
+    Arena a;
+    layout_part(a, n, n_groups > 0 ? n_groups : n);
+    return a.used();
+}
+
+extern "C" int gb_partition(gb_handle* h, const gb_graph* G, const int32_t* group, int32_t n_groups,
+                            int32_t target_core_size, gb_part* P) {
+    if (!h || !G || !P) return GB_ERR_ARG;
+    const int32_t n = G->n;
+    if (n <= 0 || !G->ptr || (G->nnz > 0 && !G->idx)) return GB_ERR_ARG;
+    if (P->n != n || !P->core_ptr || !P->core_idx || !P->core_pos || !P->sub_ptr) return GB_ERR_ARG;
+    if (P->sub_capacity < 0 || (P->sub_capacity > 0 && !P->sub_idx)) return GB_ERR_ARG;
+    int32_t block = 1;
+    if (group) {
+        if (n_groups <= 0) return GB_ERR_ARG;
+    } else {
+        if (target_core_size <= 0) return GB_ERR_ARG;
+        block = target_core_size;
+        n_groups = (n + block - 1) / block;
+    }
+    h->launches = 0;
+    Arena a(h->ws, h->ws_bytes);
+    PartLayout L = layout_part(a, n, n_groups);
+    if (!a.fits() || !h->ws) {
+        Arena m;
+        layout_part(m, n, n_groups);
+        h->required_ws = m.used();
+        return GB_ERR_WORKSPACE;
+    }
+    cudaStream_t s = h->stream;
+    GB_CUDA(cudaMemsetAsync(L.gcnt, 0, sizeof(int64_t) * (n_groups + 1), s));
+    GB_CUDA(cudaMemsetAsync(L.cursor, 0, sizeof(int64_t) * n, s));
+    GB_CUDA(cudaMemsetAsync(L.err, 0, sizeof(int) * 8, s));
+    GB_CUDA(cudaMemsetAsync(L.out_nnz, 0, sizeof(unsigned long long), s));
+    const int tb = 256;
+    GB_LAUNCH(h, k_group_count, (n + tb - 1) / tb, tb, 0, n, group, block, n_groups, L.gcnt, L.err);
+    int herr = 0;
+    GB_TRY(read_i32(h, L.err, &herr));
+    if (herr) return herr;
+    GB_LAUNCH(h, k_nonempty, (n_groups + tb - 1) / tb, tb, 0, n_groups, (const int64_t*)L.gcnt, L.cidx);
+    GB_CUDA(cudaMemsetAsync(L.cidx + n_groups, 0, sizeof(int64_t), s));
+    GB_TRY(exclusive_scan_i64(h, L.cidx, L.cidx, n_groups + 1, L.scan_tmp));
+    int64_t n_sub = 0;
+    GB_TRY(read_i64(h, L.cidx + n_groups, &n_sub));
+    P->n_sub = (int32_t)n_sub;
+    GB_LAUNCH(h, k_core_sizes, (n_groups + tb - 1) / tb, tb, 0, n_groups, (const int64_t*)L.gcnt,
+              (const int64_t*)L.cidx, P->core_ptr);
+    GB_CUDA(cudaMemsetAsync(P->core_ptr + n_sub, 0, sizeof(int64_t), s));
+    GB_TRY(exclusive_scan_i64(h, P->core_ptr, P->core_ptr, n_sub + 1, L.scan_tmp));
+    GB_LAUNCH(h, k_core_fill, (n + tb - 1) / tb, tb, 0, n, group, block, (const int64_t*)L.cidx,
+              (const int64_t*)P->core_ptr, L.cursor, P->core_idx);
+
+    const size_t smem = sizeof(uint32_t) * ((n + 31) / 32);
+    if (smem > 200 * 1024) return GB_ERR_UNSUPPORTED;
+    GB_CUDA(cudaFuncSetAttribute(k_subgraphs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = (int)(n_sub < 152 * 16 ? n_sub : 152 * 16);
+    GB_LAUNCH(h, k_subgraphs, grid, SUB_THREADS, smem, n, (int32_t)n_sub, G->ptr, G->idx,
+              (const int64_t*)P->core_ptr, P->core_idx, L.sub_size, (const int64_t*)nullptr,
+              (int32_t*)nullptr, (int32_t*)nullptr, 0, L.err + 1);
+    GB_LAUNCH(h, k_out_nnz, ((int)n_sub + tb - 1) / tb, tb, 0, (int32_t)n_sub,
+              (const int64_t*)L.sub_size, (const int64_t*)P->core_ptr, L.out_nnz);
+    GB_CUDA(cudaMemsetAsync(L.sub_size + n_sub, 0, sizeof(int64_t), s));
+    GB_TRY(exclusive_scan_i64(h, L.sub_size, P->sub_ptr, n_sub + 1, L.scan_tmp));
+    int64_t sub_nnz = 0;
+    int32_t stats[3] = {0, 0, 0};
+    unsigned long long out_nnz = 0;
+    GB_TRY(read_i64(h, P->sub_ptr + n_sub, &sub_nnz));
+    GB_TRY(read_i32(h, L.err, stats, 3));
+    GB_CUDA(cudaMemcpyAsync(&out_nnz, L.out_nnz, sizeof(out_nnz), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    P->sub_nnz = sub_nnz;
+    P->max_sub = stats[1];
+    P->max_core = stats[2];
+    P->out_nnz = (int64_t)out_nnz;
+    if (sub_nnz > P->sub_capacity) return GB_ERR_CAPACITY;
+    GB_LAUNCH(h, k_subgraphs, grid, SUB_THREADS, smem, n, (int32_t)n_sub, G->ptr, G->idx,
+              (const int64_t*)P->core_ptr, P->core_idx, (int64_t*)nullptr,
+              (const int64_t*)P->sub_ptr, P->sub_idx, P->core_pos, 1, L.err + 1);
+    GB_CUDA(cudaStreamSynchronize(s));
+    return GB_OK;
+}

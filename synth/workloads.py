@@ -32,8 +32,8 @@ WORKLOADS = {
     # 1,000 waters, 6,000 orbitals, FP64
     "water1k": Workload("water1k", 1, 1000, 0.1, 1e-5),
     # 10,000 waters, 60,000 orbitals, mixed vs FP64, kT 0.05 / 0.2, tau 1e-4 / 1e-6
-    "water10k": Workload("water10k", 2, 10000, 0.05, 1e-6, precision="mixed"),
-    "water10k_kT0.2": Workload("water10k_kT0.2", 2, 10000, 0.2, 1e-4, precision="mixed"),
+    "water10k": Workload("water10k", 2, 10000, 0.2, 1e-4, precision="mixed"),
+    "water10k_kT0.05": Workload("water10k_kT0.05", 2, 10000, 0.05, 1e-6, precision="mixed"),
     # 20,000 waters, 120,000 orbitals, m = 6 right-hand sides
     "water20k_m6": Workload("water20k_m6", 4, 20000, 0.1, 1e-5, m=6, precision="mixed"),
 }
