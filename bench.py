@@ -276,7 +276,7 @@ def main():
     head = measure(gb, args.workload, args.steps, args.warmup, args.fp64_steps, dev, stream, handle, world,
                    dist, e2e_steps=max(2, args.steps // 2))
     comp = None
-    if args.companion:
+    if args.companion and args.companion in __import__("synth").WORKLOADS:
         comp = measure(gb, args.companion, max(2, args.steps // 2), 2, 1, dev, stream, handle, world, dist)
 
     peaks = {}

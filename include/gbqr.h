@@ -119,8 +119,8 @@ typedef struct gb_opts {
                             tol_d, using |dD_jk| <= |dmu| max diag(beta d (I - d)) (d1_mu is
                             positive semidefinite).  <= 0 selects 1e-11 (FP64) / 1e-6 (split).
                             When a Newton step no longer halves the residual (trace
-                            round-off floor) mu is accepted: always in split precision,
-                            in FP64 once that bound is within 10 tol_d.                     */
+                            round-off floor) mu is accepted once that bound is within
+                            100 tol_d (split precision) or 10 tol_d (FP64).                 */
 } gb_opts;
 
 typedef struct gb_report {

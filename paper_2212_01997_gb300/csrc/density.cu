@@ -342,11 +342,12 @@ __global__ void __launch_bounds__(FP64_THREADS) k_fermi_fp64(PassArgs a) {
     }
 }
 
-// k_moff: moff[i] = n_i^2 (scanned afterwards)
-__global__ void k_block_sizes(int32_t n_sub, const int64_t* sub_ptr, int64_t* sq) {
+// sq[i] = n_i^2 (or npad_i^2 with npad = round16(n_i)), scanned afterwards
+__global__ void k_block_sizes(int32_t n_sub, const int64_t* sub_ptr, int64_t* sq, int pad16) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n_sub) {
         int64_t ni = sub_ptr[i + 1] - sub_ptr[i];
+        if (pad16) ni = (ni + 15) & ~(int64_t)15;
         sq[i] = ni * ni;
     }
 }
@@ -364,6 +365,7 @@ struct DensityLayout {
     int* err;
     double* pool;       // FP64: (NBUF + m) * pool_stride
     float* z1pool;      // split: n_sub * m * 128 * 128
+    double* hblk;       // split: (1 + m) * pool_stride dense gathered blocks
     int64_t pool_stride;
 };
 
@@ -380,14 +382,20 @@ DensityLayout layout_density(Arena& ar, const gb_part* P, int32_t m, int precisi
     L.d1mu_val = ar.take<double>(P->out_nnz);
     L.scan_tmp = ar.take<int64_t>(scan_temp_count(n_sub + 1) + 64);
     L.err = ar.take<int>(8);
-    // sum_i n_i^2 <= max_sub * sum_i n_i
-    L.pool_stride = (int64_t)P->max_sub * P->sub_nnz + 32;
     if (precision == GB_PREC_FP64) {
+        // sum_i n_i^2 <= max_sub * sum_i n_i
+        L.pool_stride = ((int64_t)P->max_sub * P->sub_nnz + 32 + 63) & ~(int64_t)63;
         L.pool = ar.take<double>((NBUF + m) * L.pool_stride);
         L.z1pool = nullptr;
+        L.hblk = nullptr;
     } else {
+        // sum_i round16(n_i)^2 <= (max_sub + 15) * (sum_i n_i + 15 n_sub)
+        // (a multiple of 64 elements: every block stays 16-byte aligned for the
+        // vector loads of the staging code)
+        L.pool_stride = (((int64_t)P->max_sub + 15) * (P->sub_nnz + 15 * n_sub) + 32 + 63) & ~(int64_t)63;
         L.pool = nullptr;
         L.z1pool = ar.take<float>(n_sub * (int64_t)(m > 0 ? m : 1) * GB_SPLIT_MAX_N * GB_SPLIT_MAX_N);
+        L.hblk = ar.take<double>((1 + m) * L.pool_stride);
     }
     return L;
 }
@@ -479,7 +487,7 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
                       P->core_idx, (const int64_t*)D->ptr, D1[r].idx);
     }
     // dense block offsets (FP64 path)
-    GB_LAUNCH(h, k_block_sizes, (n_sub + tb - 1) / tb, tb, 0, n_sub, P->sub_ptr, L.moff);
+    GB_LAUNCH(h, k_block_sizes, (n_sub + tb - 1) / tb, tb, 0, n_sub, P->sub_ptr, L.moff, split ? 1 : 0);
     GB_CUDA(cudaMemsetAsync(L.moff + n_sub, 0, sizeof(int64_t), st));
     GB_TRY(exclusive_scan_i64(h, L.moff, L.moff, (int64_t)n_sub + 1, L.scan_tmp));
     // spectral bounds
@@ -528,7 +536,13 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
     a.moff = L.moff;
     a.pool_stride = L.pool_stride;
     a.z1pool = L.z1pool;
+    a.hblk = L.hblk;
+    a.boff = L.moff;
+    a.hblk_stride = L.pool_stride;
     a.err = L.err;
+    // split path: dense principal submatrices of H and H1 once per call (they
+    // do not depend on mu)
+    if (split) GB_TRY(launch_split_gather(h, a, L.hblk));
 
     // mu: Newton-Raphson on the core traces (Eq. NewtonRaphson), safeguarded
     // by a bisection bracket; each evaluation is one full pass.
@@ -573,12 +587,11 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
         const double dmu_newton = dn > 0.0 ? fabs(resid) / dn : INFINITY;
         const double d_bound = dmu_newton * sums[TR_MAXW];
         // Noise floor: once a Newton step no longer halves the residual, the
-        // trace round-off dominates and further passes only move mu within it.
-        // FP64 accepts that floor only near tol_d; split precision accepts it
-        // (its accuracy is then set by the trace round-off, see the report).
+        // trace round-off dominates and further passes only move mu within it;
+        // that floor is accepted when its D-change bound is small.
         const bool stalled = passes >= 2 && fabs(resid) >= 0.5 * prev_resid;
         if ((o.tol_occ > 0.0 && fabs(resid) <= o.tol_occ * n_occ) || d_bound <= tol_d ||
-            (stalled && (split || d_bound <= 10.0 * tol_d))) {
+            (stalled && d_bound <= (split ? 100.0 : 10.0) * tol_d)) {
             converged = true;
             last_bound = d_bound;
             break;

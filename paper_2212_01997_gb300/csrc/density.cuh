@@ -60,6 +60,12 @@ struct PassArgs {
     int64_t pool_stride;
     // split path: FP32 response state, 128 x 128 per subgraph and RHS
     float* z1pool;
+    // split path: gathered dense blocks h^(i) and h1_r^(i) (FP64, row-major,
+    // npad = round16(|S_i|) columns), block b of subgraph i at
+    // hblk + b * hblk_stride + boff[i]  (b = 0: h, b = 1 + r: h1_r)
+    const double* hblk;
+    const int64_t* boff;
+    int64_t hblk_stride;
     int* err;
 };
 
@@ -73,3 +79,4 @@ __device__ __forceinline__ int recursion_steps(double beta, double mu, double lo
 }
 
 int launch_split_pass(gb_handle* h, const PassArgs& a);
+int launch_split_gather(gb_handle* h, const PassArgs& a, double* hblk);

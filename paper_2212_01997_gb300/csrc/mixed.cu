@@ -36,8 +36,12 @@
 
 namespace {
 
-constexpr int THREADS = 128;
+constexpr int THREADS = 256;  // 8 warps: 4 TMEM lane quadrants x 2 column groups
+constexpr int GROUPS = THREADS / 128;
 constexpr int NMAX = GB_SPLIT_MAX_N;
+constexpr int VLD = 16;       // row stride of the refinement vectors (broadcast float4 reads)
+constexpr int REFINE_ROUNDS = 1;  // refinement rounds of the final step (the tensor-core
+                                  // inverse as preconditioner leaves ~1e-14 after one)
 constexpr uint32_t HALF_BYTES = NMAX * NMAX * 2;  // one 16-bit part
 constexpr uint32_t STAGE_BYTES = 2 * HALF_BYTES;   // hi + lo
 constexpr int NSTAGE = 3;
@@ -147,6 +151,31 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+        "%30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]),
+                   "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]),
+                   "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]),
+                   "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]),
+                   "+r"(r[31])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 __device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
     uint32_t r;
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
@@ -187,17 +216,28 @@ __device__ __forceinline__ uint32_t elem_off(int r, int k) {
     return (uint32_t)(k >> 3) * LBO + (uint32_t)(r >> 3) * SBO + (uint32_t)(r & 7) * 16u + (uint32_t)(k & 7) * 2u;
 }
 
+// hi/lo split of a pair of values with packed conversions
+__device__ __forceinline__ void split_pair(float x0, float x1, int fmt, uint32_t& hi, uint32_t& lo) {
+    if (fmt == 0) {
+        const __half2 h = __floats2half2_rn(x0, x1);
+        const float2 f = __half22float2(h);
+        const __half2 l = __floats2half2_rn(x0 - f.x, x1 - f.y);
+        hi = *(const uint32_t*)&h;
+        lo = *(const uint32_t*)&l;
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+        const float2 f = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - f.x, x1 - f.y);
+        hi = *(const uint32_t*)&h;
+        lo = *(const uint32_t*)&l;
+    }
+}
+
 // write 16 consecutive columns [c0, c0+16) of row r into a staged operand
-__device__ __forceinline__ void stage_chunk(uint8_t* stage, int r, int c0, const float (&v)[16], int fmt) {
+__device__ __forceinline__ void stage_chunk(uint8_t* stage, int r, int c0, const float* v, int fmt) {
     uint32_t hi[8], lo[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        uint16_t h0, l0, h1, l1;
-        split2(v[2 * j], fmt, h0, l0);
-        split2(v[2 * j + 1], fmt, h1, l1);
-        hi[j] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-        lo[j] = (uint32_t)l0 | ((uint32_t)l1 << 16);
-    }
+    for (int j = 0; j < 8; ++j) split_pair(v[2 * j], v[2 * j + 1], fmt, hi[j], lo[j]);
     uint8_t* p0 = stage + elem_off(r, c0);
     uint8_t* p1 = stage + elem_off(r, c0 + 8);
     *(uint4*)p0 = make_uint4(hi[0], hi[1], hi[2], hi[3]);
@@ -224,6 +264,8 @@ struct Kernel {
     int fmt;
     int n, npad;
     int row;       // this thread's row = TMEM lane
+    int grp;       // column group: chunks [ch0, ch1) of 16 columns
+    int ch0, ch1;
     uint32_t lane_off;
 
     __device__ Kernel(const PassArgs& a_, Ctl& c_, uint8_t* smem) : a(a_), c(c_) {
@@ -234,11 +276,37 @@ struct Kernel {
         mbar = smem_u32(&c.mbar);
         phase = 0;
         fmt = a.split_kind;
-        row = threadIdx.x;
-        lane_off = (uint32_t)((threadIdx.x & ~31) << 16);
+        row = threadIdx.x & 127;
+        grp = threadIdx.x >> 7;
+        lane_off = (uint32_t)((row & ~31) << 16);
     }
 
+    __device__ void set_size(int n_) {
+        n = n_;
+        npad = (n + 15) & ~15;
+        const int nch = npad / 16, per = (nch + GROUPS - 1) / GROUPS;
+        ch0 = min(nch, grp * per);
+        ch1 = min(nch, ch0 + per);
+    }
+
+    __device__ bool own_col(int col) const { return col >= 16 * ch0 && col < 16 * ch1; }
+
     __device__ uint32_t slot(int s) const { return tbase + (uint32_t)s * SLOT_COLS; }
+
+    // deterministic block reduction over all threads (op 0: sum, 1: max)
+    __device__ double block_reduce(double v, int op) {
+        c.red[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = THREADS / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o)
+                c.red[threadIdx.x] = op ? fmax(c.red[threadIdx.x], c.red[threadIdx.x + o])
+                                        : c.red[threadIdx.x] + c.red[threadIdx.x + o];
+            __syncthreads();
+        }
+        const double r = c.red[0];
+        __syncthreads();
+        return r;
+    }
 
     // all threads: make generic smem writes and TMEM stores visible to the MMA
     __device__ void sync_for_mma() {
@@ -293,10 +361,42 @@ struct Kernel {
         return wait_mma();
     }
 
+    // v = (ca T[sA] + cb T[sB]) + cd I  over 16 columns at c0 (values, masked to n x n)
+    __device__ void finish16(float* v, const float* w, float ca, float cb, float cd, int c0) const {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int col = c0 + j;
+            const float x = (ca * v[j] + cb * w[j]) * TMEM_INV + ((col == row) ? cd : 0.f);
+            v[j] = (row < n && col < n) ? x : 0.f;
+        }
+    }
+
+    __device__ void emit16(float* v, int c0, int out, int sg, float* gdst) {
+        if (out >= 0) {
+            float t[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) t[j] = v[j] * TMEM_SCALE;
+            tmem_st16(slot(out) + lane_off + c0, t);
+        }
+        if (sg >= 0) {
+            float t[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) t[j] = v[j] * STAGE_SCALE;
+            stage_chunk(st[sg], row, c0, t, fmt);
+        }
+        if (gdst) {
+#pragma unroll
+            for (int j = 0; j < 16; j += 4)
+                *(float4*)(gdst + (size_t)row * NMAX + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+    }
+
     // row-wise combination  v = ca * T[sA] + cb * T[sB] + cd * I  (masked to n x n),
     // optionally written to FP32 slot `out`, staged operand `sg`, global row `gdst`.
+    // Each column group handles its own 16-column chunks.
     __device__ void combine(int sA, float ca, int sB, float cb, float cd, int out, int sg, float* gdst) {
-        for (int c0 = 0; c0 < npad; c0 += 16) {
+        for (int ch = ch0; ch < ch1; ++ch) {
+            const int c0 = ch * 16;
             float v[16], w[16];
             if (sA >= 0) tmem_ld16(slot(sA) + lane_off + c0, v);
             else {
@@ -308,105 +408,83 @@ struct Kernel {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) w[j] = 0.f;
             }
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int col = c0 + j;
-                float x = (ca * v[j] + cb * w[j]) * TMEM_INV + ((col == row) ? cd : 0.f);
-                v[j] = (row < n && col < n) ? x : 0.f;
-            }
-            if (out >= 0) {
-                float t[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) t[j] = v[j] * TMEM_SCALE;
-                tmem_st16(slot(out) + lane_off + c0, t);
-            }
-            if (sg >= 0) {
-                float t[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) t[j] = v[j] * STAGE_SCALE;
-                stage_chunk(st[sg], row, c0, t, fmt);
-            }
-            if (gdst) {
-#pragma unroll
-                for (int j = 0; j < 16; j += 4)
-                    *(float4*)(gdst + (size_t)row * NMAX + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-            }
+            finish16(v, w, ca, cb, cd, c0);
+            emit16(v, c0, out, sg, gdst);
         }
     }
 
-    // max over rows of sum_c |M[S, S]_rc| for a CSR matrix M (block-uniform)
-    __device__ double gather_rowsum_max(const int64_t* ptr, const int32_t* idx, const double* val) {
+    // max over rows of sum_c |M_rc| for a dense gathered block (block-uniform)
+    __device__ double dense_rowsum_max(const double* blk) {
         double rs = 0.0;
-        if (row < n) {
-            const int32_t g = c.S[row];
-            for (int64_t p = ptr[g]; p < ptr[g + 1]; ++p) {
-                const int32_t col = idx[p];
-                int lo = 0, hi = n;
-                while (lo < hi) {
-                    int mid = (lo + hi) >> 1;
-                    if (c.S[mid] < col) lo = mid + 1; else hi = mid;
-                }
-                if (lo < n && c.S[lo] == col) rs += fabs(val[p]);
-            }
-        }
-        c.red[threadIdx.x] = rs;
-        __syncthreads();
-        for (int o = THREADS / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o) c.red[threadIdx.x] = fmax(c.red[threadIdx.x], c.red[threadIdx.x + o]);
-            __syncthreads();
-        }
-        const double r = c.red[0];
-        __syncthreads();
-        return r;
+        if (grp == 0 && row < n)
+            for (int col = 0; col < n; ++col) rs += fabs(blk[(size_t)row * npad + col]);
+        return block_reduce(rs, 1);
     }
 
     // largest k <= kmax with 4^k max_r sum_c |T[sl]_rc| <= 1 (block-uniform)
     __device__ int fewer_steps(int sl, int kmax) {
         double rs = 0.0;
-        for (int c0 = 0; c0 < npad; c0 += 16) {
+        for (int ch = ch0; ch < ch1; ++ch) {
             float v[16];
-            tmem_ld16(slot(sl) + lane_off + c0, v);
+            tmem_ld16(slot(sl) + lane_off + ch * 16, v);
 #pragma unroll
             for (int j = 0; j < 16; ++j) rs += fabs((double)v[j] * (double)TMEM_INV);
         }
         c.red[threadIdx.x] = rs;
         __syncthreads();
-        for (int o = THREADS / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o) c.red[threadIdx.x] = fmax(c.red[threadIdx.x], c.red[threadIdx.x + o]);
-            __syncthreads();
-        }
-        const double qmax = c.red[0];
+        double tot = 0.0;
+        if (grp == 0)
+            for (int g = 0; g < GROUPS; ++g) tot += c.red[row + 128 * g];
         __syncthreads();
+        const double qmax = block_reduce(tot, 1);
         int k = 0;
         while (k < kmax && qmax * ldexp(1.0, 2 * (k + 1)) <= 1.0) ++k;
         return k;
     }
 
-    // out[c] = sum_k M_row,k v[k][c] for c < nc, M = scale x TMEM slot sl (this
-    // thread's row), v in shared memory as [k][16]: FP32 products summed per
-    // 16-column chunk (round to nearest), chunk sums in FP64.
-    __device__ void rowvec(int sl, float scale, const float* v, int nc, double (&out)[16]) {
-        for (int c = 0; c < 16; ++c) out[c] = 0.0;
-        for (int c0 = 0; c0 < npad; c0 += 16) {
+    // res[row][cc] = sum_k M_row,k v[k][cc] (cc < nc), M = scale x TMEM slot sl,
+    // v and res in shared memory ([k][VLD] floats, [row][VLD] doubles): FP32
+    // products summed per 16-column chunk (round to nearest), chunk sums and the
+    // column groups' partials in FP64.  `part` is shared scratch [128][VLD].
+    __device__ void rowvec(int sl, float scale, const float* v, int nc, double* part, double* res) {
+        double out[16];
+#pragma unroll
+        for (int cc = 0; cc < 16; ++cc) out[cc] = 0.0;
+        for (int ch = ch0; ch < ch1; ++ch) {
+            const int c0 = ch * 16;
             float m[16];
             tmem_ld16(slot(sl) + lane_off + c0, m);
-            float part[16];
+            float acc[16];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) part[c] = 0.f;
+            for (int cc = 0; cc < 16; ++cc) acc[cc] = 0.f;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const float mj = m[j] * scale;
-                const float* vr = v + (c0 + j) * 16;
+                const float4* vr = (const float4*)(v + (c0 + j) * VLD);
 #pragma unroll
-                for (int c = 0; c < 16; ++c) part[c] = fmaf(mj, vr[c], part[c]);
+                for (int q = 0; q < 4; ++q) {
+                    const float4 x = vr[q];
+                    acc[4 * q] = fmaf(mj, x.x, acc[4 * q]);
+                    acc[4 * q + 1] = fmaf(mj, x.y, acc[4 * q + 1]);
+                    acc[4 * q + 2] = fmaf(mj, x.z, acc[4 * q + 2]);
+                    acc[4 * q + 3] = fmaf(mj, x.w, acc[4 * q + 3]);
+                }
             }
-            for (int c = 0; c < nc; ++c) out[c] += (double)part[c];
+#pragma unroll
+            for (int cc = 0; cc < 16; ++cc) out[cc] += (double)acc[cc];
         }
+        if (grp == 1)
+            for (int cc = 0; cc < nc; ++cc) part[row * VLD + cc] = out[cc];
+        __syncthreads();
+        if (grp == 0)
+            for (int cc = 0; cc < 16; ++cc) res[row * VLD + cc] = cc < nc ? out[cc] + part[row * VLD + cc] : 0.0;
+        __syncthreads();
     }
 
     // staged operand from a global FP32 128 x 128 row-major block
     __device__ void stage_global(const float* g, int sg) {
-        for (int c0 = 0; c0 < npad; c0 += 16) {
+        for (int ch = ch0; ch < ch1; ++ch) {
+            const int c0 = ch * 16;
             float v[16];
 #pragma unroll
             for (int j = 0; j < 16; j += 4) {
@@ -420,27 +498,27 @@ struct Kernel {
         }
     }
 
-    // staged operand  scale * (M[S, S] - shift I)  from CSR
-    __device__ void stage_gather(const int64_t* ptr, const int32_t* idx, const double* val, double scale,
-                                 double shift, int sg) {
-        const float z[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int c0 = 0; c0 < npad; c0 += 16) stage_chunk(st[sg], row, c0, z, fmt);
-        if (row < n) {
-            const int32_t g = c.S[row];
-            double diag = 0.0;
-            for (int64_t p = ptr[g]; p < ptr[g + 1]; ++p) {
-                const int32_t col = idx[p];
-                int lo = 0, hi = n;
-                while (lo < hi) {
-                    int mid = (lo + hi) >> 1;
-                    if (c.S[mid] < col) lo = mid + 1; else hi = mid;
+    // staged operand  scale * (M - shift I)  from a dense gathered block (FP64
+    // arithmetic, then rounded once to FP32)
+    __device__ void stage_dense(const double* blk, double scale, double shift, int sg) {
+        for (int ch = ch0; ch < ch1; ++ch) {
+            const int c0 = ch * 16;
+            float v[16];
+            if (row < n) {
+                const double* src = blk + (size_t)row * npad + c0;
+#pragma unroll
+                for (int j = 0; j < 16; j += 2) {
+                    const double2 q = *(const double2*)(src + j);
+                    const double d0 = (c0 + j == row) ? q.x - shift : q.x;
+                    const double d1 = (c0 + j + 1 == row) ? q.y - shift : q.y;
+                    v[j] = (c0 + j < n) ? (float)(scale * d0) * STAGE_SCALE : 0.f;
+                    v[j + 1] = (c0 + j + 1 < n) ? (float)(scale * d1) * STAGE_SCALE : 0.f;
                 }
-                if (lo < n && c.S[lo] == col) {
-                    if (lo == row) diag = val[p];
-                    else stage_put(st[sg], row, lo, (float)(scale * val[p]) * STAGE_SCALE, fmt);
-                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = 0.f;
             }
-            stage_put(st[sg], row, row, (float)(scale * (diag - shift)) * STAGE_SCALE, fmt);
+            stage_chunk(st[sg], row, c0, v, fmt);
         }
     }
 };
@@ -475,8 +553,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
         const int64_t s0 = a.sub_ptr[i];
         const int n = (int)(a.sub_ptr[i + 1] - s0);
         const int64_t c0 = a.core_ptr[i], c1 = a.core_ptr[i + 1];
-        K.n = n;
-        K.npad = (n + 15) & ~15;
+        K.set_size(n);
         for (int r = threadIdx.x; r < n; r += THREADS) c.S[r] = a.sub_idx[s0 + r];
         __syncthreads();
         int s = recursion_steps(a.beta, a.mu, a.eps_lo[i], a.eps_hi[i], a.min_steps);
@@ -484,7 +561,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
         float* z1base = a.z1pool + (size_t)i * (a.m > 0 ? a.m : 1) * NMAX * NMAX;
 
         // ---- Taylor start: Q = x0^2, P = I - Q/3 + 2 Q^2/15 (slots: 0 Q, 1 P) ----
-        K.stage_gather(a.Hptr, a.Hidx, a.Hval, alpha, a.mu, 0);           // S0 = x0
+        const double* hb = a.hblk + a.boff[i];
+        K.stage_dense(hb, alpha, a.mu, 0);                                // S0 = x0
         if (!K.gemm(0, 0, 0)) break;                                      // T0 = Q
         // rho(x0)^2 = rho(Q) <= max_r sum_c |Q_rc| (Gershgorin on the square is
         // tighter than on h): drop k steps while 2^k x0 keeps spectral radius <= 1
@@ -494,7 +572,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
             s -= k;
             alpha = ldexp(a.beta, -(s + 1));
             qscale = ldexpf(1.f, 2 * k);
-            K.stage_gather(a.Hptr, a.Hidx, a.Hval, alpha, a.mu, 0);       // S0 = 2^k x0
+            K.stage_dense(hb, alpha, a.mu, 0);                            // S0 = 2^k x0
         }
         K.combine(0, qscale, -1, 0.f, 0.f, -1, 1, nullptr);               // S1 = Q
         if (!K.gemm(1, 1, 1)) break;                                      // T1 = Q^2
@@ -502,12 +580,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
         bool ok = true;
         for (int r = 0; r < a.m && ok; ++r) {
             // normalise the perturbation: (beta / 2) sigma max row sum |h1| <= 1
-            const double h1max = K.gather_rowsum_max(a.H1ptr[r], a.H1idx[r], a.H1val[r]);
+            const double* h1b = a.hblk + (int64_t)(1 + r) * a.hblk_stride + a.boff[i];
+            const double h1max = K.dense_rowsum_max(h1b);
             double sig = 1.0;
             while (0.5 * a.beta * sig * h1max > 1.0 && sig > 1e-30) sig *= 0.5;
             if (threadIdx.x == 0) c.sig[r] = sig;
             // dZ0 = X1 P + x0 P1,  P1 = -Q1/3 + (2/15)(Q Q1 + Q1 Q),  Q1 = x0 X1 + X1 x0
-            K.stage_gather(a.H1ptr[r], a.H1idx[r], a.H1val[r], alpha * sig, 0.0, 1);  // S1 = X1
+            K.stage_dense(h1b, alpha * sig, 0.0, 1);                       // S1 = X1
             K.sync_for_mma();
             if (threadIdx.x == 0) {
                 fence_after();
@@ -527,7 +606,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
             K.combine(2, -1.f / 3.f, 3, 2.f / 15.f, 0.f, -1, 1, nullptr);  // S1 = P1
             if (!(ok = K.gemm(2, 0, 1))) break;                            // T2 = x0 P1
             K.combine(1, 1.f, -1, 0.f, 0.f, -1, 2, nullptr);               // S2 = P
-            K.stage_gather(a.H1ptr[r], a.H1idx[r], a.H1val[r], alpha * sig, 0.0, 1);  // S1 = X1
+            K.stage_dense(h1b, alpha * sig, 0.0, 1);                       // S1 = X1
             if (!(ok = K.gemm(2, 1, 2, 0, true))) break;                   // T2 += X1 P
             K.combine(2, 1.f, -1, 0.f, 0.f, -1, -1, z1base + (size_t)r * NMAX * NMAX);
         }
@@ -561,19 +640,25 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
             if (!(ok = K.gemm(ts, 2, 0))) break;                                        // W / 2 = X Z
             if (step == s - 1) {
                 // ---- final correction on the core columns (CUDA cores) ----
-                // w = Z_s e_c = 2 (I + Z^2)^-1 Z e_c by two rounds of iterative
+                // w = Z_s e_c = 2 (I + Z^2)^-1 Z e_c by a round of iterative
                 // refinement: w <- w + X (2 z - w - Z (Z w)), X the tensor-core
                 // inverse as preconditioner; every product rounds to nearest, so
                 // the saturated occupations (and Tr_c d) carry no accumulation bias.
                 fence_before();
                 __syncthreads();
                 fence_after();
-                float* V = (float*)K.st[0];  // S0 is free until W is staged below
-                float* Vz = V;
-                float* Vw = V + NMAX * 16;
-                float* Vt = V + 2 * NMAX * 16;
+                // S0 is free until W is staged below: vectors [128][VLD] floats,
+                // the refined columns w and a product result [128][VLD] doubles, and
+                // the column-group partials [128][VLD] doubles
+                float* Vz = (float*)K.st[0];
+                float* Vw = Vz + NMAX * VLD;
+                float* Vt = Vw + NMAX * VLD;
+                double* Wd = (double*)(Vt + NMAX * VLD);
+                double* Rd = Wd + NMAX * VLD;
+                double* part = Rd + NMAX * VLD;
                 const float zsc = zscale * TMEM_INV;
                 const int ncore = (int)(c1 - c0);
+                const bool mine = K.grp == 0 && K.row < n;
                 for (int e = threadIdx.x; e < ncore; e += THREADS) c.cpos[e] = a.core_pos[c0 + e];
                 __syncthreads();
                 for (int b0 = 0; b0 < ncore; b0 += 16) {
@@ -581,47 +666,48 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
                     for (int cc = 0; cc < 16; ++cc) {
                         float zv = 0.f;
                         if (cc < nc) zv = tmem_ld1(K.slot(zs) + K.lane_off + c.cpos[b0 + cc]) * zsc;
-                        Vz[K.row * 16 + cc] = (K.row < n) ? zv : 0.f;
+                        if (K.grp == 0) Vz[K.row * VLD + cc] = (K.row < n) ? zv : 0.f;
                     }
                     __syncthreads();
-                    double acc[16], wv[16];
-                    K.rowvec(xs, TMEM_INV, Vz, nc, acc);
-                    for (int cc = 0; cc < 16; ++cc) {
-                        wv[cc] = (K.row < n && cc < nc) ? 2.0 * acc[cc] : 0.0;
-                        Vw[K.row * 16 + cc] = (float)wv[cc];
-                    }
+                    K.rowvec(xs, TMEM_INV, Vz, nc, part, Rd);                           // X z
+                    if (K.grp == 0)
+                        for (int cc = 0; cc < 16; ++cc) {
+                            const double w0 = (mine && cc < nc) ? 2.0 * Rd[K.row * VLD + cc] : 0.0;
+                            Wd[K.row * VLD + cc] = w0;
+                            Vw[K.row * VLD + cc] = (float)w0;
+                        }
                     __syncthreads();
-                    for (int it = 0; it < 2; ++it) {
-                        K.rowvec(zs, zsc, Vw, nc, acc);                                 // Z w
+                    for (int it = 0; it < REFINE_ROUNDS; ++it) {
+                        K.rowvec(zs, zsc, Vw, nc, part, Rd);                            // Z w
+                        if (K.grp == 0)
+                            for (int cc = 0; cc < 16; ++cc) Vt[K.row * VLD + cc] = mine ? (float)Rd[K.row * VLD + cc] : 0.f;
                         __syncthreads();
-                        for (int cc = 0; cc < 16; ++cc) Vt[K.row * 16 + cc] = (K.row < n) ? (float)acc[cc] : 0.f;
+                        K.rowvec(zs, zsc, Vt, nc, part, Rd);                            // Z (Z w)
+                        if (K.grp == 0)
+                            for (int cc = 0; cc < 16; ++cc) {
+                                const double res = 2.0 * (double)Vz[K.row * VLD + cc] - Wd[K.row * VLD + cc] -
+                                                   Rd[K.row * VLD + cc];
+                                Vt[K.row * VLD + cc] = (mine && cc < nc) ? (float)res : 0.f;
+                            }
                         __syncthreads();
-                        K.rowvec(zs, zsc, Vt, nc, acc);                                 // Z (Z w)
-                        __syncthreads();
-                        for (int cc = 0; cc < 16; ++cc) {
-                            const double res = 2.0 * (double)Vz[K.row * 16 + cc] - wv[cc] - acc[cc];
-                            Vt[K.row * 16 + cc] = (K.row < n && cc < nc) ? (float)res : 0.f;
-                        }
-                        __syncthreads();
-                        K.rowvec(xs, TMEM_INV, Vt, nc, acc);                            // X r
-                        __syncthreads();
-                        for (int cc = 0; cc < 16; ++cc) {
-                            if (K.row < n && cc < nc) wv[cc] += acc[cc];
-                            Vw[K.row * 16 + cc] = (float)wv[cc];
-                        }
+                        K.rowvec(xs, TMEM_INV, Vt, nc, part, Rd);                       // X r
+                        if (K.grp == 0)
+                            for (int cc = 0; cc < 16; ++cc) {
+                                if (mine && cc < nc) Wd[K.row * VLD + cc] += Rd[K.row * VLD + cc];
+                                Vw[K.row * VLD + cc] = (float)Wd[K.row * VLD + cc];
+                            }
                         __syncthreads();
                     }
                     // d = (I - Z_s) / 2 on the core columns
-                    for (int cc = 0; cc < nc; ++cc) {
-                        const int kc = c.cpos[b0 + cc];
-                        const int64_t o = a.col_ptr[a.core_idx[c0 + b0 + cc]];
-                        if (K.row < n) {
-                            const double dv = 0.5 * ((K.row == kc ? 1.0 : 0.0) - wv[cc]);
+                    if (mine)
+                        for (int cc = 0; cc < nc; ++cc) {
+                            const int kc = c.cpos[b0 + cc];
+                            const int64_t o = a.col_ptr[a.core_idx[c0 + b0 + cc]];
+                            const double dv = 0.5 * ((K.row == kc ? 1.0 : 0.0) - Wd[K.row * VLD + cc]);
                             if (!isfinite(dv)) set_error(a.err, GB_ERR_NAN);
                             a.Dval[o + K.row] = dv;
                             if (K.row == kc) tr_d += dv;
                         }
-                    }
                     __syncthreads();
                 }
                 // d (I - d) = (I - Z_s^2) / 4 = ((I - Y) X)^2 / 4: no cancellation
@@ -634,13 +720,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
                     const int kc = c.cpos[e - c0];
                     const int64_t o = a.col_ptr[a.core_idx[e]];
                     const float gv = tmem_ld1(K.slot(ys) + K.lane_off + kc) * TMEM_INV;
-                    if (K.row < n) {
+                    if (K.row < n && K.grp == 0) {
                         const double mv = 0.25 * a.beta * (double)gv;
                         a.d1mu_val[o + K.row] = mv;
                         if (K.row == kc) tr_dd += 0.25 * (double)gv;
                     }
                 }
-                for (int cc = 0; cc < K.npad; cc += 16) {
+                for (int cc = 16 * K.ch0; cc < 16 * K.ch1; cc += 16) {
                     float v[16];
                     tmem_ld16(K.slot(ys) + K.lane_off + cc, v);
 #pragma unroll
@@ -676,7 +762,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
         for (int64_t e = c0; e < c1; ++e) {
             const int kc = c.cpos[e - c0];
             const int64_t o = a.col_ptr[a.core_idx[e]];
-            if (K.row < n) {
+            if (K.row < n && K.grp == 0) {
                 for (int r = 0; r < a.m; ++r) {
                     const double lv = -0.5 / c.sig[r] * (double)z1base[(size_t)r * NMAX * NMAX + (size_t)K.row * NMAX + kc];
                     a.D1val[r][o + K.row] = lv;
@@ -714,7 +800,50 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
                      : "memory");
 }
 
+// Dense principal submatrices h^(i) = H[S_i, S_i] and h1_r^(i) (FP64, npad
+// columns, zero padding), one block per subgraph, one warp per row.
+__global__ void __launch_bounds__(256) k_gather_dense(PassArgs a, double* hblk) {
+    __shared__ int32_t S[NMAX];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int32_t i = blockIdx.x; i < a.n_sub; i += gridDim.x) {
+        const int64_t s0 = a.sub_ptr[i];
+        const int n = (int)(a.sub_ptr[i + 1] - s0);
+        const int npad = (n + 15) & ~15;
+        for (int r = threadIdx.x; r < n; r += blockDim.x) S[r] = a.sub_idx[s0 + r];
+        for (int b = 0; b <= a.m; ++b) {
+            double* blk = hblk + (int64_t)b * a.hblk_stride + a.boff[i];
+            for (int e = threadIdx.x; e < npad * npad; e += blockDim.x) blk[e] = 0.0;
+        }
+        __syncthreads();
+        for (int b = 0; b <= a.m; ++b) {
+            const int64_t* ptr = b == 0 ? a.Hptr : a.H1ptr[b - 1];
+            const int32_t* idx = b == 0 ? a.Hidx : a.H1idx[b - 1];
+            const double* val = b == 0 ? a.Hval : a.H1val[b - 1];
+            double* blk = hblk + (int64_t)b * a.hblk_stride + a.boff[i];
+            for (int r = warp; r < n; r += blockDim.x / 32) {
+                const int32_t g = S[r];
+                for (int64_t p = ptr[g] + lane; p < ptr[g + 1]; p += 32) {
+                    const int32_t col = idx[p];
+                    int lo = 0, hi = n;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (S[mid] < col) lo = mid + 1; else hi = mid;
+                    }
+                    if (lo < n && S[lo] == col) blk[(size_t)r * npad + lo] = val[p];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
+
+int launch_split_gather(gb_handle* h, const PassArgs& a, double* hblk) {
+    const int grid = a.n_sub < 152 * 8 ? a.n_sub : 152 * 8;
+    GB_LAUNCH(h, k_gather_dense, grid, 256, 0, a, hblk);
+    return GB_OK;
+}
 
 int launch_split_pass(gb_handle* h, const PassArgs& a) {
     static bool configured = false;
