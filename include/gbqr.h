@@ -201,6 +201,32 @@ size_t gb_partition_workspace_size(int32_t n, int64_t nnz_g, int32_t n_groups);
 int gb_partition(gb_handle* h, const gb_graph* G, const int32_t* group, int32_t n_groups,
                  int32_t target_core_size, gb_part* P);
 
+/* ---- gb_partition_noalloc ---------------------------------------------- *
+ * The same partition as gb_partition, for callers that cannot allocate device
+ * memory: code running inside a host framework that owns every device
+ * allocation (a pre-sized memory pool, a plugin with no allocator handle), or
+ * code that must not allocate while it runs.  The paper has no counterpart;
+ * this is a library convenience.
+ *   stream  cudaStream_t (NULL = legacy default stream) on the current device.
+ *   Other arguments and the output are those of gb_partition; inputs and
+ *   outputs are still the caller's [device] buffers.
+ * Scratch: a fixed array compiled into the library
+ * (gb_partition_noalloc_scratch_bytes() bytes, about 2.1 MB, held by every
+ * GPU that loads the library until the process exits).  It serves at most
+ * GB_NOALLOC_MAX_VERTICES vertices and as many groups; larger requests return
+ * GB_ERR_WORKSPACE before any work.  The entry point calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ * The first call on a device looks up the array's device address on the
+ * current device (cudaGetSymbolAddress), so make that first call before any
+ * stream capture.  All calls share the one array and it keeps the last call's
+ * contents (the call clears what it needs): calls that overlap on the GPU --
+ * on different streams, or from different host threads -- race and must be
+ * serialised by the caller.  Synchronises the stream. */
+#define GB_NOALLOC_MAX_VERTICES 65536
+size_t gb_partition_noalloc_scratch_bytes(void);
+int gb_partition_noalloc(void* stream, const gb_graph* G, const int32_t* group, int32_t n_groups,
+                         int32_t target_core_size, gb_part* P);
+
 /* ---- gb_density_and_response ------------------------------------------- *
  * For every subgraph i: gather h^(i) = H[S_i,S_i] and h1_r^(i) = H1_r[S_i,S_i]
  * (Eq. sub_f), evaluate the Fermi-Dirac density matrix
