@@ -365,7 +365,9 @@ struct DensityLayout {
     int* err;
     double* pool;       // FP64: (NBUF + m) * pool_stride
     float* z1pool;      // split: n_sub * m * 128 * 128
-    double* hblk;       // split: (1 + m) * pool_stride dense gathered blocks
+    float* hblk;        // split: (1 + m) * pool_stride dense gathered blocks (FP32)
+    double* hdiag;      // split: sub_nnz FP64 diagonals of h^(i)
+    double* h1max;      // split: n_sub * m largest |h1| row sums
     int64_t pool_stride;
 };
 
@@ -388,6 +390,8 @@ DensityLayout layout_density(Arena& ar, const gb_part* P, int32_t m, int precisi
         L.pool = ar.take<double>((NBUF + m) * L.pool_stride);
         L.z1pool = nullptr;
         L.hblk = nullptr;
+        L.hdiag = nullptr;
+        L.h1max = nullptr;
     } else {
         // sum_i round16(n_i)^2 <= (max_sub + 15) * (sum_i n_i + 15 n_sub)
         // (a multiple of 64 elements: every block stays 16-byte aligned for the
@@ -395,7 +399,9 @@ DensityLayout layout_density(Arena& ar, const gb_part* P, int32_t m, int precisi
         L.pool_stride = (((int64_t)P->max_sub + 15) * (P->sub_nnz + 15 * n_sub) + 32 + 63) & ~(int64_t)63;
         L.pool = nullptr;
         L.z1pool = ar.take<float>(n_sub * (int64_t)(m > 0 ? m : 1) * GB_SPLIT_MAX_N * GB_SPLIT_MAX_N);
-        L.hblk = ar.take<double>((1 + m) * L.pool_stride);
+        L.hblk = ar.take<float>((1 + m) * L.pool_stride);
+        L.hdiag = ar.take<double>(P->sub_nnz);
+        L.h1max = ar.take<double>(n_sub * (int64_t)(m > 0 ? m : 1));
     }
     return L;
 }
@@ -539,10 +545,12 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
     a.hblk = L.hblk;
     a.boff = L.moff;
     a.hblk_stride = L.pool_stride;
+    a.hdiag = L.hdiag;
+    a.h1max = L.h1max;
     a.err = L.err;
     // split path: dense principal submatrices of H and H1 once per call (they
     // do not depend on mu)
-    if (split) GB_TRY(launch_split_gather(h, a, L.hblk));
+    if (split) GB_TRY(launch_split_gather(h, a, L.hblk, L.hdiag));
 
     // mu: Newton-Raphson on the core traces (Eq. NewtonRaphson), safeguarded
     // by a bisection bracket; each evaluation is one full pass.

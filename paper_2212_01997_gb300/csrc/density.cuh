@@ -60,12 +60,19 @@ struct PassArgs {
     int64_t pool_stride;
     // split path: FP32 response state, 128 x 128 per subgraph and RHS
     float* z1pool;
-    // split path: gathered dense blocks h^(i) and h1_r^(i) (FP64, row-major,
-    // npad = round16(|S_i|) columns), block b of subgraph i at
-    // hblk + b * hblk_stride + boff[i]  (b = 0: h, b = 1 + r: h1_r)
-    const double* hblk;
+    // split path: gathered dense blocks beta h^(i) and beta h1_r^(i) (FP32, each
+    // rounded once from the FP64 product), npad = round16(|S_i|) rows and
+    // columns, stored in column groups of four: element (r, c) at
+    // ((c / 4) * npad + r) * 4 + c % 4, so a warp reading one group of 32 rows
+    // reads 512 contiguous bytes.  Block b of subgraph i is at
+    // hblk + b * hblk_stride + boff[i] (b = 0: h, b = 1 + r: h1_r).
+    const float* hblk;
     const int64_t* boff;
     int64_t hblk_stride;
+    // split path: FP64 diagonal of h^(i), at hdiag[sub_ptr[i] + r]
+    const double* hdiag;
+    // split path: largest row sum of |h1_r^(i)|, at h1max[i * m + r]
+    double* h1max;
     int* err;
 };
 
@@ -79,4 +86,4 @@ __device__ __forceinline__ int recursion_steps(double beta, double mu, double lo
 }
 
 int launch_split_pass(gb_handle* h, const PassArgs& a);
-int launch_split_gather(gb_handle* h, const PassArgs& a, double* hblk);
+int launch_split_gather(gb_handle* h, const PassArgs& a, float* hblk, double* hdiag);

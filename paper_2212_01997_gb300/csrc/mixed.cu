@@ -27,8 +27,11 @@
 //   repeat: (I - X) -> ts; ts += -Y X; stage R -> S0; xs += X R; stage X -> S2;
 //   stage Z -> S0; W/2 = X Z -> ts;
 //   per RHS: stage W -> S0, Z1 -> S1; X Z1 -> ys, W Z1 -> zs;
-//            Z1' = (2 X Z1) X - (W Z1 / 2) W -> ys -> global FP32;
+//            Z1' = (2 X Z1) X - (W Z1 / 2) W -> ys -> global FP32
+//            (last step: only its core columns, as d1_lambda);
 //   new Z = 2 * ts.
+// The last step also redoes Z_s on the core columns on the CUDA cores (see
+// refine_core) and forms d1_mu = beta ((I - Y) X)^2 / 4.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -39,7 +42,6 @@ namespace {
 constexpr int THREADS = 256;  // 8 warps: 4 TMEM lane quadrants x 2 column groups
 constexpr int GROUPS = THREADS / 128;
 constexpr int NMAX = GB_SPLIT_MAX_N;
-constexpr int VLD = 16;       // row stride of the refinement vectors (broadcast float4 reads)
 constexpr int REFINE_ROUNDS = 1;  // refinement rounds of the final step (the tensor-core
                                   // inverse as preconditioner leaves ~1e-14 after one)
 constexpr uint32_t HALF_BYTES = NMAX * NMAX * 2;  // one 16-bit part
@@ -58,8 +60,8 @@ struct __align__(16) Ctl {
     unsigned long long mbar;
     uint32_t tmem_base;
     int abort;
-    int32_t S[NMAX];
-    int32_t cpos[NMAX];
+    int32_t cpos[NMAX];     // core vertices' positions in S_i
+    int64_t ocol[NMAX];     // their columns' offsets in the collected CSC outputs
     double red[THREADS];
     double sig[GB_MAX_RHS];  // per-RHS perturbation normalisation of the current subgraph
 };
@@ -151,36 +153,50 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+// two 16-column loads (e.g. the same chunk of two slots) behind one wait
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float (&u)[16], float (&w)[16]) {
+    uint32_t r[16], q[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-        "%30, %31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
-                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]),
-                   "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]),
-                   "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]),
-                   "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]),
-                   "+r"(r[31])
-                 :
-                 : "memory");
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(ta));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15}, [%16];"
+        : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]),
+          "=r"(q[7]), "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]),
+          "=r"(q[14]), "=r"(q[15])
+        : "r"(tb));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    // the registers are defined only after the wait: pin every use behind it
 #pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+    for (int j = 0; j < 16; ++j) asm volatile("" : "+r"(r[j]), "+r"(q[j]));
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        u[j] = __uint_as_float(r[j]);
+        w[j] = __uint_as_float(q[j]);
+    }
 }
 
-__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
-    uint32_t r;
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r) : : "memory");
-    return __uint_as_float(r);
+// one column per RHS of a block: NC single-column loads (columns cols[q],
+// q < nc; the others repeat cols[0]) behind one wait.  Warp-uniform columns.
+template <int NC>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t base, const int32_t* cols, int nc, float (&v)[NC]) {
+    uint32_t r[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+        const uint32_t col = (uint32_t)cols[q < nc ? q : 0];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r[q]) : "r"(base + col));
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+        asm volatile("" : "+r"(r[q]));
+        v[q] = __uint_as_float(r[q]);
+    }
 }
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
@@ -194,22 +210,11 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) 
         "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
         "r"(__float_as_uint(v[15]))
         : "memory");
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-// hi/lo split of one value into 16-bit parts (fmt 0: FP16, 1: BF16)
-__device__ __forceinline__ void split2(float x, int fmt, uint16_t& hi, uint16_t& lo) {
-    if (fmt == 0) {
-        __half h = __float2half_rn(x);
-        __half l = __float2half_rn(x - __half2float(h));
-        hi = __half_as_ushort(h);
-        lo = __half_as_ushort(l);
-    } else {
-        __nv_bfloat16 h = __float2bfloat16_rn(x);
-        __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-        hi = __bfloat16_as_ushort(h);
-        lo = __bfloat16_as_ushort(l);
-    }
+// completes every tcgen05.st this thread issued
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ uint32_t elem_off(int r, int k) {
@@ -244,13 +249,6 @@ __device__ __forceinline__ void stage_chunk(uint8_t* stage, int r, int c0, const
     *(uint4*)p1 = make_uint4(hi[4], hi[5], hi[6], hi[7]);
     *(uint4*)(p0 + HALF_BYTES) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     *(uint4*)(p1 + HALF_BYTES) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
-}
-
-__device__ __forceinline__ void stage_put(uint8_t* stage, int r, int k, float x, int fmt) {
-    uint16_t h, l;
-    split2(x, fmt, h, l);
-    *(uint16_t*)(stage + elem_off(r, k)) = h;
-    *(uint16_t*)(stage + elem_off(r, k) + HALF_BYTES) = l;
 }
 
 struct Kernel {
@@ -289,9 +287,8 @@ struct Kernel {
         ch1 = min(nch, ch0 + per);
     }
 
-    __device__ bool own_col(int col) const { return col >= 16 * ch0 && col < 16 * ch1; }
-
     __device__ uint32_t slot(int s) const { return tbase + (uint32_t)s * SLOT_COLS; }
+    __device__ static int c0_of(int ch) { return ch * 16; }
 
     // deterministic block reduction over all threads (op 0: sum, 1: max)
     __device__ double block_reduce(double v, int op) {
@@ -361,108 +358,108 @@ struct Kernel {
         return wait_mma();
     }
 
-    // v = (ca T[sA] + cb T[sB]) + cd I  over 16 columns at c0 (values, masked to n x n)
-    __device__ void finish16(float* v, const float* w, float ca, float cb, float cd, int c0) const {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int col = c0 + j;
-            const float x = (ca * v[j] + cb * w[j]) * TMEM_INV + ((col == row) ? cd : 0.f);
-            v[j] = (row < n && col < n) ? x : 0.f;
-        }
-    }
-
-    __device__ void emit16(float* v, int c0, int out, int sg, float* gdst) {
-        if (out >= 0) {
-            float t[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) t[j] = v[j] * TMEM_SCALE;
-            tmem_st16(slot(out) + lane_off + c0, t);
-        }
-        if (sg >= 0) {
-            float t[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) t[j] = v[j] * STAGE_SCALE;
-            stage_chunk(st[sg], row, c0, t, fmt);
-        }
-        if (gdst) {
-#pragma unroll
-            for (int j = 0; j < 16; j += 4)
-                *(float4*)(gdst + (size_t)row * NMAX + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-        }
-    }
-
-    // row-wise combination  v = ca * T[sA] + cb * T[sB] + cd * I  (masked to n x n),
-    // optionally written to FP32 slot `out`, staged operand `sg`, global row `gdst`.
-    // Each column group handles its own 16-column chunks.
+    // Row-wise combination over this thread's 16-column chunks:
+    //   u = ca T[sA] + cb T[sB] + cd I   (cd on the diagonal of the n x n block)
+    // written to FP32 slot `out` (TMEM units), staged operand `sg` and/or the
+    // global FP32 128 x 128 block `gdst` (values, in column groups of four:
+    // element (r, c) at ((c / 4) * 128 + r) * 4 + c % 4); sB = -1 drops the
+    // second term.  Every
+    // slot is exactly zero outside the n x n block (the staged operands are),
+    // so only the identity needs masking.  The power-of-two unit changes are
+    // folded into the coefficients.
     __device__ void combine(int sA, float ca, int sB, float cb, float cd, int out, int sg, float* gdst) {
+        const bool stage_only = out < 0 && gdst == nullptr;
+        const float unit = stage_only ? STAGE_SCALE * TMEM_INV : 1.f;
+        const float ka = ca * unit, kb = cb * unit, kd = cd * TMEM_SCALE * unit;
+        const bool diag = cd != 0.f && row < n;
         for (int ch = ch0; ch < ch1; ++ch) {
             const int c0 = ch * 16;
-            float v[16], w[16];
-            if (sA >= 0) tmem_ld16(slot(sA) + lane_off + c0, v);
-            else {
+            float u[16];
+            if (sB >= 0) {
+                float w[16];
+                tmem_ld16x2(slot(sA) + lane_off + c0, slot(sB) + lane_off + c0, u, w);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = 0.f;
-            }
-            if (sB >= 0) tmem_ld16(slot(sB) + lane_off + c0, w);
-            else {
+                for (int j = 0; j < 16; ++j) u[j] = fmaf(kb, w[j], ka * u[j]);
+            } else {
+                tmem_ld16(slot(sA) + lane_off + c0, u);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) w[j] = 0.f;
+                for (int j = 0; j < 16; ++j) u[j] *= ka;
             }
-            finish16(v, w, ca, cb, cd, c0);
-            emit16(v, c0, out, sg, gdst);
+            if (diag && (unsigned)(row - c0) < 16u) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (c0 + j == row) u[j] += kd;
+            }
+            if (out >= 0) tmem_st16(slot(out) + lane_off + c0, u);
+            if (sg >= 0) {
+                if (stage_only) {
+                    stage_chunk(st[sg], row, c0, u, fmt);
+                } else {
+                    float t[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) t[j] = u[j] * (STAGE_SCALE * TMEM_INV);
+                    stage_chunk(st[sg], row, c0, t, fmt);
+                }
+            }
+            if (gdst) {
+#pragma unroll
+                for (int j = 0; j < 16; j += 4)
+                    *(float4*)(gdst + ((size_t)((c0 + j) >> 2) * NMAX + row) * 4) =
+                        make_float4(u[j] * TMEM_INV, u[j + 1] * TMEM_INV, u[j + 2] * TMEM_INV, u[j + 3] * TMEM_INV);
+            }
         }
+        if (out >= 0) tmem_wait_st();
     }
 
-    // max over rows of sum_c |M_rc| for a dense gathered block (block-uniform)
-    __device__ double dense_rowsum_max(const double* blk) {
-        double rs = 0.0;
-        if (grp == 0 && row < n)
-            for (int col = 0; col < n; ++col) rs += fabs(blk[(size_t)row * npad + col]);
-        return block_reduce(rs, 1);
-    }
-
-    // largest k <= kmax with 4^k max_r sum_c |T[sl]_rc| <= 1 (block-uniform)
+    // largest k <= kmax with 4^k max_r sum_c |T[sl]_rc| <= 1 (block-uniform).
+    // Row sums in FP32; the factor 1 + 2^-16 covers their rounding, so the
+    // bound stays an upper bound.
     __device__ int fewer_steps(int sl, int kmax) {
-        double rs = 0.0;
+        float rs = 0.f;
         for (int ch = ch0; ch < ch1; ++ch) {
             float v[16];
             tmem_ld16(slot(sl) + lane_off + ch * 16, v);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) rs += fabs((double)v[j] * (double)TMEM_INV);
+            for (int j = 0; j < 16; ++j) rs += fabsf(v[j]);
         }
-        c.red[threadIdx.x] = rs;
+        c.red[threadIdx.x] = (double)rs;
         __syncthreads();
         double tot = 0.0;
         if (grp == 0)
             for (int g = 0; g < GROUPS; ++g) tot += c.red[row + 128 * g];
         __syncthreads();
-        const double qmax = block_reduce(tot, 1);
+        const double qmax = block_reduce(tot * (double)TMEM_INV, 1) * (1.0 + 0x1p-16);
         int k = 0;
         while (k < kmax && qmax * ldexp(1.0, 2 * (k + 1)) <= 1.0) ++k;
         return k;
     }
 
-    // res[row][cc] = sum_k M_row,k v[k][cc] (cc < nc), M = scale x TMEM slot sl,
-    // v and res in shared memory ([k][VLD] floats, [row][VLD] doubles): FP32
-    // products summed per 16-column chunk (round to nearest), chunk sums and the
-    // column groups' partials in FP64.  `part` is shared scratch [128][VLD].
-    __device__ void rowvec(int sl, float scale, const float* v, int nc, double* part, double* res) {
-        double out[16];
+    // Matrix times NC vectors on the CUDA cores: P_g[cc][row] = sum over this
+    // column group's k of M_row,k v[k][cc], M = scale x TMEM slot sl.  v is in
+    // shared memory as [k][NC + 4] floats (broadcast float4 reads); FP32
+    // products are summed per 16-column chunk (round to nearest), the chunk
+    // sums without rounding error (float pairs, then FP64).  P holds the two groups' partials, [2][NC][NMAX] doubles
+    // (column-major, so the row-indexed stores are conflict-free); the caller
+    // adds P_0 + P_1 after a barrier.
+    template <int NC>
+    __device__ void rowvec(int sl, float scale, const float* v, double* P) {
+        constexpr int VL = NC + 4;
+        float hi[NC], lo[NC];  // chunk sums accumulated as unevaluated float pairs
 #pragma unroll
-        for (int cc = 0; cc < 16; ++cc) out[cc] = 0.0;
+        for (int cc = 0; cc < NC; ++cc) hi[cc] = lo[cc] = 0.f;
         for (int ch = ch0; ch < ch1; ++ch) {
             const int c0 = ch * 16;
             float m[16];
             tmem_ld16(slot(sl) + lane_off + c0, m);
-            float acc[16];
+            float acc[NC];
 #pragma unroll
-            for (int cc = 0; cc < 16; ++cc) acc[cc] = 0.f;
+            for (int cc = 0; cc < NC; ++cc) acc[cc] = 0.f;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const float mj = m[j] * scale;
-                const float4* vr = (const float4*)(v + (c0 + j) * VLD);
+                const float4* vr = (const float4*)(v + (c0 + j) * VL);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < NC / 4; ++q) {
                     const float4 x = vr[q];
                     acc[4 * q] = fmaf(mj, x.x, acc[4 * q]);
                     acc[4 * q + 1] = fmaf(mj, x.y, acc[4 * q + 1]);
@@ -471,52 +468,209 @@ struct Kernel {
                 }
             }
 #pragma unroll
-            for (int cc = 0; cc < 16; ++cc) out[cc] += (double)acc[cc];
+            for (int cc = 0; cc < NC; ++cc) {  // error-free sum (Knuth's TwoSum)
+                const float t = hi[cc] + acc[cc];
+                const float bv = t - hi[cc];
+                lo[cc] += (hi[cc] - (t - bv)) + (acc[cc] - bv);
+                hi[cc] = t;
+            }
         }
-        if (grp == 1)
-            for (int cc = 0; cc < nc; ++cc) part[row * VLD + cc] = out[cc];
-        __syncthreads();
-        if (grp == 0)
-            for (int cc = 0; cc < 16; ++cc) res[row * VLD + cc] = cc < nc ? out[cc] + part[row * VLD + cc] : 0.0;
-        __syncthreads();
+        double* Pg = P + grp * (NC * NMAX);
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc) Pg[cc * NMAX + row] = (double)hi[cc] + (double)lo[cc];
     }
 
-    // staged operand from a global FP32 128 x 128 row-major block
+    // row `row` of NC float vectors, [row][NC + 4] (16-byte stores, conflict-free)
+    template <int NC>
+    __device__ void put_row(float* V, const float* x) {
+        constexpr int VL = NC + 4;
+#pragma unroll
+        for (int q = 0; q < NC / 4; ++q)
+            *(float4*)(V + row * VL + 4 * q) = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+    }
+
+    // The last doubling on the core columns, on CUDA cores: w = Z_s e_c =
+    // 2 (I + Z^2)^-1 Z e_c by iterative refinement with the tensor-core
+    // inverse X as preconditioner,  w <- w + X (2 z - w - Z (Z w)),  every
+    // product rounded to nearest.  The saturated occupations (and Tr_c d) then
+    // carry no accumulation bias.  Writes d = (I - Z_s)/2 on the core columns.
+    // Scratch: staged operands S0 and S1 (free at this point).  All threads.
+    template <int NC>
+    __device__ void refine_core(int zs, int xs, float zsc, int ncore, double& tr_d) {
+        constexpr int VL = NC + 4;
+        float* Vz = (float*)st[0];
+        float* Vw = Vz + NMAX * VL;
+        float* Vt = Vw + NMAX * VL;
+        double* Wd = (double*)(Vt + NMAX * VL);  // [NC][NMAX]
+        double* P = Wd + NC * NMAX;              // [2][NC][NMAX]
+        const double* P1 = P + NC * NMAX;
+        const bool live = grp == 0 && row < n;
+        for (int b0 = 0; b0 < ncore; b0 += NC) {
+            const int nc = min(NC, ncore - b0);
+            float x[NC];
+            if (grp == 0) {
+                float zv[NC];
+                tmem_ld_cols<NC>(slot(zs) + lane_off, c.cpos + b0, nc, zv);
+#pragma unroll
+                for (int cc = 0; cc < NC; ++cc) x[cc] = (row < n && cc < nc) ? zv[cc] * zsc : 0.f;
+                put_row<NC>(Vz, x);
+            }
+            __syncthreads();
+            rowvec<NC>(xs, TMEM_INV, Vz, P);                                   // X z
+            __syncthreads();
+            if (grp == 0) {
+#pragma unroll
+                for (int cc = 0; cc < NC; ++cc) {
+                    const double w0 = (live && cc < nc) ? 2.0 * (P[cc * NMAX + row] + P1[cc * NMAX + row]) : 0.0;
+                    Wd[cc * NMAX + row] = w0;
+                    x[cc] = (float)w0;
+                }
+                put_row<NC>(Vw, x);
+            }
+            __syncthreads();
+            for (int it = 0; it < REFINE_ROUNDS; ++it) {
+                rowvec<NC>(zs, zsc, Vw, P);                                     // Z w
+                __syncthreads();
+                if (grp == 0) {
+#pragma unroll
+                    for (int cc = 0; cc < NC; ++cc)
+                        x[cc] = live ? (float)(P[cc * NMAX + row] + P1[cc * NMAX + row]) : 0.f;
+                    put_row<NC>(Vt, x);
+                }
+                __syncthreads();
+                rowvec<NC>(zs, zsc, Vt, P);                                     // Z (Z w)
+                __syncthreads();
+                if (grp == 0) {
+#pragma unroll
+                    for (int cc = 0; cc < NC; ++cc) {
+                        const double res = 2.0 * (double)Vz[row * VL + cc] - Wd[cc * NMAX + row] -
+                                           (P[cc * NMAX + row] + P1[cc * NMAX + row]);
+                        x[cc] = (live && cc < nc) ? (float)res : 0.f;
+                    }
+                    put_row<NC>(Vt, x);
+                }
+                __syncthreads();
+                rowvec<NC>(xs, TMEM_INV, Vt, P);                                // X r
+                __syncthreads();
+                if (grp == 0) {
+#pragma unroll
+                    for (int cc = 0; cc < NC; ++cc) {
+                        double w = Wd[cc * NMAX + row];
+                        if (live && cc < nc) w += P[cc * NMAX + row] + P1[cc * NMAX + row];
+                        Wd[cc * NMAX + row] = w;
+                        x[cc] = (float)w;
+                    }
+                    put_row<NC>(Vw, x);
+                }
+                __syncthreads();
+            }
+            if (live) {
+                for (int cc = 0; cc < nc; ++cc) {
+                    const int kc = c.cpos[b0 + cc];
+                    const double dv = 0.5 * ((row == kc ? 1.0 : 0.0) - Wd[cc * NMAX + row]);
+                    if (!isfinite(dv)) set_error(a.err, GB_ERR_NAN);
+                    a.Dval[c.ocol[b0 + cc] + row] = dv;
+                    if (row == kc) tr_d += dv;
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    // core columns of slot sl (TMEM units) times `scale` into out[ocol + row];
+    // `tr` collects the core diagonal (times tscale).  Warps of column group 0.
+    __device__ void core_columns(int sl, int ncore, double scale, double* out, double tscale, double& tr) {
+        if (grp != 0) return;
+        for (int b0 = 0; b0 < ncore; b0 += 16) {
+            const int nc = min(16, ncore - b0);
+            float g[16];
+            tmem_ld_cols<16>(slot(sl) + lane_off, c.cpos + b0, nc, g);
+            if (row < n) {
+#pragma unroll
+                for (int cc = 0; cc < 16; ++cc) {
+                    if (cc < nc) {
+                        const double v = (double)g[cc] * (double)TMEM_INV;
+                        out[c.ocol[b0 + cc] + row] = scale * v;
+                        if (row == c.cpos[b0 + cc]) tr += tscale * v;
+                    }
+                }
+            }
+        }
+    }
+
+    // element (row, row) of slot sl in values (warps of column group 0, rows < n)
+    __device__ double diag_elem(int sl) {
+        if (grp != 0) return 0.0;
+        const uint32_t cb = (uint32_t)(row & ~31);
+        float u[16], w[16];
+        tmem_ld16x2(slot(sl) + lane_off + cb, slot(sl) + lane_off + cb + 16, u, w);
+        float d = 0.f;
+        const int j = row & 31;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            d = (j == q) ? u[q] : d;
+            d = (j == q + 16) ? w[q] : d;
+        }
+        return row < n ? (double)d * (double)TMEM_INV : 0.0;
+    }
+
+    // pull the next subgraph's gathered blocks toward L2 while this one runs
+    __device__ void prefetch_blocks(int32_t i) {
+        if (i >= a.n_sub) return;
+        const int64_t ni = a.sub_ptr[i + 1] - a.sub_ptr[i];
+        const int64_t np = (ni + 15) & ~(int64_t)15;
+        const int64_t bytes = np * np * (int64_t)sizeof(float);
+        for (int b = 0; b <= a.m; ++b) {
+            const char* base = (const char*)(a.hblk + (int64_t)b * a.hblk_stride + a.boff[i]);
+            for (int64_t o = (int64_t)threadIdx.x * 128; o < bytes; o += (int64_t)THREADS * 128)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(base + o));
+        }
+    }
+
+    // staged operand from a global FP32 128 x 128 block in column groups of
+    // four (element (r, c) at ((c / 4) * 128 + r) * 4 + c % 4; coalesced)
     __device__ void stage_global(const float* g, int sg) {
         for (int ch = ch0; ch < ch1; ++ch) {
-            const int c0 = ch * 16;
             float v[16];
 #pragma unroll
-            for (int j = 0; j < 16; j += 4) {
-                float4 q = *(const float4*)(g + (size_t)row * NMAX + c0 + j);
-                v[j] = q.x * STAGE_SCALE;
-                v[j + 1] = q.y * STAGE_SCALE;
-                v[j + 2] = q.z * STAGE_SCALE;
-                v[j + 3] = q.w * STAGE_SCALE;
+            for (int q = 0; q < 4; ++q) {
+                const float4 x = *(const float4*)(g + ((size_t)(4 * ch + q) * NMAX + row) * 4);
+                v[4 * q] = x.x * STAGE_SCALE;
+                v[4 * q + 1] = x.y * STAGE_SCALE;
+                v[4 * q + 2] = x.z * STAGE_SCALE;
+                v[4 * q + 3] = x.w * STAGE_SCALE;
             }
-            stage_chunk(st[sg], row, c0, v, fmt);
+            stage_chunk(st[sg], row, c0_of(ch), v, fmt);
         }
     }
 
-    // staged operand  scale * (M - shift I)  from a dense gathered block (FP64
-    // arithmetic, then rounded once to FP32)
-    __device__ void stage_dense(const double* blk, double scale, double shift, int sg) {
+    // staged operand from a gathered block beta M (FP32, column groups of four):
+    // scale x blk, scale = 2^-(s+1) [x sigma] (exact power of two), and on the
+    // diagonal, when diag != nullptr, alpha (diag - shift) in FP64 rounded once
+    __device__ void stage_dense(const float* blk, float scale, const double* diag, double alpha, double shift, int sg) {
+        const float k = scale * STAGE_SCALE;
+        const bool has_diag = diag != nullptr && row < n;
+        const float dv = has_diag ? (float)(alpha * (diag[row] - shift)) * STAGE_SCALE : 0.f;
         for (int ch = ch0; ch < ch1; ++ch) {
-            const int c0 = ch * 16;
+            const int c0 = c0_of(ch);
             float v[16];
-            if (row < n) {
-                const double* src = blk + (size_t)row * npad + c0;
+            if (row < npad) {
 #pragma unroll
-                for (int j = 0; j < 16; j += 2) {
-                    const double2 q = *(const double2*)(src + j);
-                    const double d0 = (c0 + j == row) ? q.x - shift : q.x;
-                    const double d1 = (c0 + j + 1 == row) ? q.y - shift : q.y;
-                    v[j] = (c0 + j < n) ? (float)(scale * d0) * STAGE_SCALE : 0.f;
-                    v[j + 1] = (c0 + j + 1 < n) ? (float)(scale * d1) * STAGE_SCALE : 0.f;
+                for (int q = 0; q < 4; ++q) {
+                    const float4 x = *(const float4*)(blk + ((size_t)(4 * ch + q) * npad + row) * 4);
+                    v[4 * q] = x.x * k;
+                    v[4 * q + 1] = x.y * k;
+                    v[4 * q + 2] = x.z * k;
+                    v[4 * q + 3] = x.w * k;
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) v[j] = 0.f;
+            }
+            if (has_diag && (unsigned)(row - c0) < 16u) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (c0 + j == row) v[j] = dv;
             }
             stage_chunk(st[sg], row, c0, v, fmt);
         }
@@ -554,15 +708,21 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
         const int n = (int)(a.sub_ptr[i + 1] - s0);
         const int64_t c0 = a.core_ptr[i], c1 = a.core_ptr[i + 1];
         K.set_size(n);
-        for (int r = threadIdx.x; r < n; r += THREADS) c.S[r] = a.sub_idx[s0 + r];
+        const int ncore = (int)(c1 - c0);
+        for (int e = threadIdx.x; e < ncore; e += THREADS) {
+            c.cpos[e] = a.core_pos[c0 + e];
+            c.ocol[e] = a.col_ptr[a.core_idx[c0 + e]];
+        }
+        K.prefetch_blocks(i + (int32_t)gridDim.x);
         __syncthreads();
         int s = recursion_steps(a.beta, a.mu, a.eps_lo[i], a.eps_hi[i], a.min_steps);
         double alpha = ldexp(a.beta, -(s + 1));
         float* z1base = a.z1pool + (size_t)i * (a.m > 0 ? a.m : 1) * NMAX * NMAX;
 
         // ---- Taylor start: Q = x0^2, P = I - Q/3 + 2 Q^2/15 (slots: 0 Q, 1 P) ----
-        const double* hb = a.hblk + a.boff[i];
-        K.stage_dense(hb, alpha, a.mu, 0);                                // S0 = x0
+        const float* hb = a.hblk + a.boff[i];
+        const double* hd = a.hdiag + s0;
+        K.stage_dense(hb, ldexpf(1.f, -(s + 1)), hd, alpha, a.mu, 0);     // S0 = x0
         if (!K.gemm(0, 0, 0)) break;                                      // T0 = Q
         // rho(x0)^2 = rho(Q) <= max_r sum_c |Q_rc| (Gershgorin on the square is
         // tighter than on h): drop k steps while 2^k x0 keeps spectral radius <= 1
@@ -572,7 +732,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
             s -= k;
             alpha = ldexp(a.beta, -(s + 1));
             qscale = ldexpf(1.f, 2 * k);
-            K.stage_dense(hb, alpha, a.mu, 0);                            // S0 = 2^k x0
+            K.stage_dense(hb, ldexpf(1.f, -(s + 1)), hd, alpha, a.mu, 0); // S0 = 2^k x0
         }
         K.combine(0, qscale, -1, 0.f, 0.f, -1, 1, nullptr);               // S1 = Q
         if (!K.gemm(1, 1, 1)) break;                                      // T1 = Q^2
@@ -580,13 +740,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
         bool ok = true;
         for (int r = 0; r < a.m && ok; ++r) {
             // normalise the perturbation: (beta / 2) sigma max row sum |h1| <= 1
-            const double* h1b = a.hblk + (int64_t)(1 + r) * a.hblk_stride + a.boff[i];
-            const double h1max = K.dense_rowsum_max(h1b);
+            const float* h1b = a.hblk + (int64_t)(1 + r) * a.hblk_stride + a.boff[i];
+            const double h1max = a.h1max[(int64_t)i * a.m + r];
             double sig = 1.0;
             while (0.5 * a.beta * sig * h1max > 1.0 && sig > 1e-30) sig *= 0.5;
             if (threadIdx.x == 0) c.sig[r] = sig;
             // dZ0 = X1 P + x0 P1,  P1 = -Q1/3 + (2/15)(Q Q1 + Q1 Q),  Q1 = x0 X1 + X1 x0
-            K.stage_dense(h1b, alpha * sig, 0.0, 1);                       // S1 = X1
+            K.stage_dense(h1b, (float)ldexp(sig, -(s + 1)), nullptr, 0.0, 0.0, 1);  // S1 = X1
             K.sync_for_mma();
             if (threadIdx.x == 0) {
                 fence_after();
@@ -606,7 +766,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
             K.combine(2, -1.f / 3.f, 3, 2.f / 15.f, 0.f, -1, 1, nullptr);  // S1 = P1
             if (!(ok = K.gemm(2, 0, 1))) break;                            // T2 = x0 P1
             K.combine(1, 1.f, -1, 0.f, 0.f, -1, 2, nullptr);               // S2 = P
-            K.stage_dense(h1b, alpha * sig, 0.0, 1);                       // S1 = X1
+            K.stage_dense(h1b, (float)ldexp(sig, -(s + 1)), nullptr, 0.0, 0.0, 1);  // S1 = X1
             if (!(ok = K.gemm(2, 1, 2, 0, true))) break;                   // T2 += X1 P
             K.combine(2, 1.f, -1, 0.f, 0.f, -1, -1, z1base + (size_t)r * NMAX * NMAX);
         }
@@ -615,6 +775,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
         if (!K.gemm(2, 0, 2)) break;                                      // T2 = Z0 = x0 P
 
         // ---- doublings ----
+        double tr_l[GB_MAX_RHS];
+        for (int r = 0; r < a.m; ++r) tr_l[r] = 0.0;
         int zs = 2;
         float zscale = 1.f;
         double tr_d = 0.0, tr_dd = 0.0, wmax = 0.0;
@@ -639,100 +801,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
             K.combine(zs, zscale, -1, 0.f, 0.f, -1, 0, nullptr);                        // S0 = Z
             if (!(ok = K.gemm(ts, 2, 0))) break;                                        // W / 2 = X Z
             if (step == s - 1) {
-                // ---- final correction on the core columns (CUDA cores) ----
-                // w = Z_s e_c = 2 (I + Z^2)^-1 Z e_c by a round of iterative
-                // refinement: w <- w + X (2 z - w - Z (Z w)), X the tensor-core
-                // inverse as preconditioner; every product rounds to nearest, so
-                // the saturated occupations (and Tr_c d) carry no accumulation bias.
-                fence_before();
-                __syncthreads();
-                fence_after();
-                // S0 is free until W is staged below: vectors [128][VLD] floats,
-                // the refined columns w and a product result [128][VLD] doubles, and
-                // the column-group partials [128][VLD] doubles
-                float* Vz = (float*)K.st[0];
-                float* Vw = Vz + NMAX * VLD;
-                float* Vt = Vw + NMAX * VLD;
-                double* Wd = (double*)(Vt + NMAX * VLD);
-                double* Rd = Wd + NMAX * VLD;
-                double* part = Rd + NMAX * VLD;
+                // ---- the last doubling redone on the core columns (CUDA cores) ----
                 const float zsc = zscale * TMEM_INV;
-                const int ncore = (int)(c1 - c0);
-                const bool mine = K.grp == 0 && K.row < n;
-                for (int e = threadIdx.x; e < ncore; e += THREADS) c.cpos[e] = a.core_pos[c0 + e];
-                __syncthreads();
-                for (int b0 = 0; b0 < ncore; b0 += 16) {
-                    const int nc = min(16, ncore - b0);
-                    for (int cc = 0; cc < 16; ++cc) {
-                        float zv = 0.f;
-                        if (cc < nc) zv = tmem_ld1(K.slot(zs) + K.lane_off + c.cpos[b0 + cc]) * zsc;
-                        if (K.grp == 0) Vz[K.row * VLD + cc] = (K.row < n) ? zv : 0.f;
-                    }
-                    __syncthreads();
-                    K.rowvec(xs, TMEM_INV, Vz, nc, part, Rd);                           // X z
-                    if (K.grp == 0)
-                        for (int cc = 0; cc < 16; ++cc) {
-                            const double w0 = (mine && cc < nc) ? 2.0 * Rd[K.row * VLD + cc] : 0.0;
-                            Wd[K.row * VLD + cc] = w0;
-                            Vw[K.row * VLD + cc] = (float)w0;
-                        }
-                    __syncthreads();
-                    for (int it = 0; it < REFINE_ROUNDS; ++it) {
-                        K.rowvec(zs, zsc, Vw, nc, part, Rd);                            // Z w
-                        if (K.grp == 0)
-                            for (int cc = 0; cc < 16; ++cc) Vt[K.row * VLD + cc] = mine ? (float)Rd[K.row * VLD + cc] : 0.f;
-                        __syncthreads();
-                        K.rowvec(zs, zsc, Vt, nc, part, Rd);                            // Z (Z w)
-                        if (K.grp == 0)
-                            for (int cc = 0; cc < 16; ++cc) {
-                                const double res = 2.0 * (double)Vz[K.row * VLD + cc] - Wd[K.row * VLD + cc] -
-                                                   Rd[K.row * VLD + cc];
-                                Vt[K.row * VLD + cc] = (mine && cc < nc) ? (float)res : 0.f;
-                            }
-                        __syncthreads();
-                        K.rowvec(xs, TMEM_INV, Vt, nc, part, Rd);                       // X r
-                        if (K.grp == 0)
-                            for (int cc = 0; cc < 16; ++cc) {
-                                if (mine && cc < nc) Wd[K.row * VLD + cc] += Rd[K.row * VLD + cc];
-                                Vw[K.row * VLD + cc] = (float)Wd[K.row * VLD + cc];
-                            }
-                        __syncthreads();
-                    }
-                    // d = (I - Z_s) / 2 on the core columns
-                    if (mine)
-                        for (int cc = 0; cc < nc; ++cc) {
-                            const int kc = c.cpos[b0 + cc];
-                            const int64_t o = a.col_ptr[a.core_idx[c0 + b0 + cc]];
-                            const double dv = 0.5 * ((K.row == kc ? 1.0 : 0.0) - Wd[K.row * VLD + cc]);
-                            if (!isfinite(dv)) set_error(a.err, GB_ERR_NAN);
-                            a.Dval[o + K.row] = dv;
-                            if (K.row == kc) tr_d += dv;
-                        }
-                    __syncthreads();
-                }
+                if (ncore <= 8) K.refine_core<8>(zs, xs, zsc, ncore, tr_d);
+                else K.refine_core<16>(zs, xs, zsc, ncore, tr_d);
                 // d (I - d) = (I - Z_s^2) / 4 = ((I - Y) X)^2 / 4: no cancellation
                 // near saturation (Y = Z_{s-1}^2, X = (I + Y)^-1)
                 K.combine(ys, -1.f, -1, 0.f, 1.f, -1, 1, nullptr);                      // S1 = I - Y
                 if (!(ok = K.gemm(zs, 1, 2))) break;                                    // G = (I - Y) X
                 K.combine(zs, 1.f, -1, 0.f, 0.f, -1, 1, nullptr);                       // S1 = G
                 if (!(ok = K.gemm(ys, 1, 1))) break;                                    // G^2
-                for (int e = c0; e < c1; ++e) {
-                    const int kc = c.cpos[e - c0];
-                    const int64_t o = a.col_ptr[a.core_idx[e]];
-                    const float gv = tmem_ld1(K.slot(ys) + K.lane_off + kc) * TMEM_INV;
-                    if (K.row < n && K.grp == 0) {
-                        const double mv = 0.25 * a.beta * (double)gv;
-                        a.d1mu_val[o + K.row] = mv;
-                        if (K.row == kc) tr_dd += 0.25 * (double)gv;
-                    }
-                }
-                for (int cc = 16 * K.ch0; cc < 16 * K.ch1; cc += 16) {
-                    float v[16];
-                    tmem_ld16(K.slot(ys) + K.lane_off + cc, v);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (cc + j == K.row && K.row < n) wmax = 0.25 * a.beta * (double)v[j] * (double)TMEM_INV;
-                }
+                K.core_columns(ys, ncore, 0.25 * a.beta, a.d1mu_val, 0.25, tr_dd);     // d1_mu = beta G^2 / 4
+                wmax = 0.25 * a.beta * K.diag_elem(ys);
             }
             if (a.m > 0) K.combine(ts, 2.f, -1, 0.f, 0.f, -1, 0, nullptr);              // S0 = W
             for (int r = 0; r < a.m && ok; ++r) {
@@ -749,43 +829,42 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
                 if (!(ok = K.gemm(ys, 1, 2))) break;                                    // 2 X Z1 X
                 K.combine(zs, -0.5f, -1, 0.f, 0.f, -1, 1, nullptr);                     // S1 = -W Z1 / 2
                 if (!(ok = K.gemm(ys, 1, 0, 0, true))) break;                           // - W Z1 W / 2
-                K.combine(ys, 1.f, -1, 0.f, 0.f, -1, -1, z1);                           // Z1 -> global
+                if (step < s - 1) {
+                    K.combine(ys, 1.f, -1, 0.f, 0.f, -1, -1, z1);                       // Z1 -> global
+                } else {
+                    const double sc = -0.5 / c.sig[r];                                  // d1_lambda = -Z1_s / (2 sigma)
+                    K.core_columns(ys, ncore, sc, a.D1val[r], sc, tr_l[r]);
+                }
             }
             zs = ts;
             zscale = 2.f;
         }
         if (!ok) break;
 
-        // ---- d1_lambda = -Z1_s / (2 sigma) on the core columns ----
-        double tr_l[GB_MAX_RHS];
-        for (int r = 0; r < a.m; ++r) tr_l[r] = 0.0;
-        for (int64_t e = c0; e < c1; ++e) {
-            const int kc = c.cpos[e - c0];
-            const int64_t o = a.col_ptr[a.core_idx[e]];
-            if (K.row < n && K.grp == 0) {
-                for (int r = 0; r < a.m; ++r) {
-                    const double lv = -0.5 / c.sig[r] * (double)z1base[(size_t)r * NMAX * NMAX + (size_t)K.row * NMAX + kc];
-                    a.D1val[r][o + K.row] = lv;
-                    if (K.row == kc) tr_l[r] += lv;
-                }
+        // per-subgraph core traces: warp shuffles, then the warps' partials in a
+        // fixed order (deterministic)
+        const int nslot = TR_FIXED + a.m;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int sl = 0; sl < nslot; ++sl) {
+            double v = sl == TR_D ? tr_d : sl == TR_DD ? tr_dd : sl == TR_D1MU ? a.beta * tr_dd
+                     : sl == TR_FLOPS ? (threadIdx.x == 0 ? pass_gemm_flops(n, s, a.ns_iters, a.m) : 0.0)
+                     : sl == TR_MAXW ? wmax
+                                     : tr_l[sl - TR_D1LAM];
+            for (int o = 16; o > 0; o >>= 1) {
+                const double t = __shfl_down_sync(0xffffffffu, v, o);
+                v = sl == TR_MAXW ? fmax(v, t) : v + t;
             }
+            if (lane == 0) c.red[sl * (THREADS / 32) + warp] = v;
         }
-        // per-subgraph core traces (fixed-order block reduction)
-        for (int slot = 0; slot < TR_FIXED + a.m; ++slot) {
-            double v = slot == TR_D ? tr_d : slot == TR_DD ? tr_dd : slot == TR_D1MU ? a.beta * tr_dd
-                     : slot == TR_FLOPS ? (threadIdx.x == 0 ? pass_gemm_flops(n, s, a.ns_iters, a.m) : 0.0)
-                     : slot == TR_MAXW ? wmax
-                                        : tr_l[slot - TR_D1LAM];
-            c.red[threadIdx.x] = v;
-            __syncthreads();
-            for (int o = THREADS / 2; o > 0; o >>= 1) {
-                if (threadIdx.x < o)
-                    c.red[threadIdx.x] = slot == TR_MAXW ? fmax(c.red[threadIdx.x], c.red[threadIdx.x + o])
-                                                         : c.red[threadIdx.x] + c.red[threadIdx.x + o];
-                __syncthreads();
+        __syncthreads();
+        if (threadIdx.x < nslot) {
+            const int sl = threadIdx.x;
+            double v = c.red[sl * (THREADS / 32)];
+            for (int w = 1; w < THREADS / 32; ++w) {
+                const double t = c.red[sl * (THREADS / 32) + w];
+                v = sl == TR_MAXW ? fmax(v, t) : v + t;
             }
-            if (threadIdx.x == 0) a.tr[(int64_t)i * a.tr_stride + slot] = c.red[0];
-            __syncthreads();
+            a.tr[(int64_t)i * a.tr_stride + sl] = v;
         }
         if (threadIdx.x == 0) a.steps_out[i] = s;
         fence_before();
@@ -800,28 +879,37 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
                      : "memory");
 }
 
-// Dense principal submatrices h^(i) = H[S_i, S_i] and h1_r^(i) (FP64, npad
-// columns, zero padding), one block per subgraph, one warp per row.
-__global__ void __launch_bounds__(256) k_gather_dense(PassArgs a, double* hblk) {
+// Dense principal submatrices beta h^(i) = beta H[S_i, S_i] and beta h1_r^(i)
+// (FP32 in column groups of four, zero padding to npad), the FP64 diagonal of
+// h^(i), one block per subgraph, one warp per row.  Also the
+// largest row sum of |h1_r^(i)| (h1max[i * m + r]), which fixes the
+// perturbation's normalisation in the recursion.
+__global__ void __launch_bounds__(256) k_gather_dense(PassArgs a, float* hblk, double* hdiag) {
     __shared__ int32_t S[NMAX];
+    __shared__ double wmax[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int32_t i = blockIdx.x; i < a.n_sub; i += gridDim.x) {
         const int64_t s0 = a.sub_ptr[i];
         const int n = (int)(a.sub_ptr[i + 1] - s0);
         const int npad = (n + 15) & ~15;
-        for (int r = threadIdx.x; r < n; r += blockDim.x) S[r] = a.sub_idx[s0 + r];
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+            S[r] = a.sub_idx[s0 + r];
+            hdiag[s0 + r] = 0.0;
+        }
         for (int b = 0; b <= a.m; ++b) {
-            double* blk = hblk + (int64_t)b * a.hblk_stride + a.boff[i];
-            for (int e = threadIdx.x; e < npad * npad; e += blockDim.x) blk[e] = 0.0;
+            float* blk = hblk + (int64_t)b * a.hblk_stride + a.boff[i];
+            for (int e = threadIdx.x; e < npad * npad; e += blockDim.x) blk[e] = 0.f;
         }
         __syncthreads();
         for (int b = 0; b <= a.m; ++b) {
             const int64_t* ptr = b == 0 ? a.Hptr : a.H1ptr[b - 1];
             const int32_t* idx = b == 0 ? a.Hidx : a.H1idx[b - 1];
             const double* val = b == 0 ? a.Hval : a.H1val[b - 1];
-            double* blk = hblk + (int64_t)b * a.hblk_stride + a.boff[i];
+            float* blk = hblk + (int64_t)b * a.hblk_stride + a.boff[i];
+            double rmax = 0.0;
             for (int r = warp; r < n; r += blockDim.x / 32) {
                 const int32_t g = S[r];
+                double rs = 0.0;
                 for (int64_t p = ptr[g] + lane; p < ptr[g + 1]; p += 32) {
                     const int32_t col = idx[p];
                     int lo = 0, hi = n;
@@ -829,8 +917,24 @@ __global__ void __launch_bounds__(256) k_gather_dense(PassArgs a, double* hblk) 
                         const int mid = (lo + hi) >> 1;
                         if (S[mid] < col) lo = mid + 1; else hi = mid;
                     }
-                    if (lo < n && S[lo] == col) blk[(size_t)r * npad + lo] = val[p];
+                    if (lo < n && S[lo] == col) {
+                        const double x = val[p];
+                        blk[((size_t)(lo >> 2) * npad + r) * 4 + (lo & 3)] = (float)(a.beta * x);
+                        if (b == 0 && lo == r) hdiag[s0 + r] = x;
+                        rs += fabs(x);
+                    }
                 }
+                rmax = fmax(rmax, warp_sum(rs));  // lane 0 holds the row sum
+            }
+            if (b > 0) {
+                if (lane == 0) wmax[warp] = rmax;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    double v = wmax[0];
+                    for (int w = 1; w < (int)(blockDim.x / 32); ++w) v = fmax(v, wmax[w]);
+                    a.h1max[(int64_t)i * a.m + (b - 1)] = v;
+                }
+                __syncthreads();
             }
         }
         __syncthreads();
@@ -839,9 +943,9 @@ __global__ void __launch_bounds__(256) k_gather_dense(PassArgs a, double* hblk) 
 
 }  // namespace
 
-int launch_split_gather(gb_handle* h, const PassArgs& a, double* hblk) {
+int launch_split_gather(gb_handle* h, const PassArgs& a, float* hblk, double* hdiag) {
     const int grid = a.n_sub < 152 * 8 ? a.n_sub : 152 * 8;
-    GB_LAUNCH(h, k_gather_dense, grid, 256, 0, a, hblk);
+    GB_LAUNCH(h, k_gather_dense, grid, 256, 0, a, hblk, hdiag);
     return GB_OK;
 }
 
