@@ -56,14 +56,22 @@ constexpr float STAGE_SCALE = 4096.f;               // staged operand = 2^12 x v
 constexpr float TMEM_SCALE = 16777216.f;            // TMEM word = 2^24 x value
 constexpr float TMEM_INV = 1.f / 16777216.f;
 
+// per-core-vertex trace terms (FP32 values, summed in FP64 at the end)
+enum CoreTerm { T_DHI = 0, T_DLO = 1, T_DD = 2, T_L0 = 3, T_COUNT = 3 + GB_MAX_RHS };
+
 struct __align__(16) Ctl {
     unsigned long long mbar;
     uint32_t tmem_base;
     int abort;
-    int32_t cpos[NMAX];     // core vertices' positions in S_i
-    int64_t ocol[NMAX];     // their columns' offsets in the collected CSC outputs
-    double red[THREADS];
-    double sig[GB_MAX_RHS];  // per-RHS perturbation normalisation of the current subgraph
+    int s;                      // the current subgraph's step count
+    int kfew;                   // steps dropped by the bound on Q
+    int32_t sigk[GB_MAX_RHS];   // perturbation normalisation sigma_r = 2^-sigk[r]
+    int32_t cpos[NMAX];         // core vertices' positions in S_i
+    int64_t ocol[NMAX];         // their columns' offsets in the collected CSC outputs
+    float dg[NMAX];             // diagonal of x0 = alpha (h - mu) (FP64, rounded once)
+    float red[THREADS];
+    float wred[THREADS / 32];
+    float tv[T_COUNT][NMAX];    // d (hi, lo), G^2/4 and d1_lambda_r on the core diagonal
 };
 
 constexpr size_t SMEM_BYTES = NSTAGE * STAGE_BYTES + sizeof(Ctl) + 1024;
@@ -251,6 +259,34 @@ __device__ __forceinline__ void stage_chunk(uint8_t* stage, int r, int c0, const
     *(uint4*)(p1 + HALF_BYTES) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
 }
 
+// float -> double by integer operations (exact; FP32 subnormals flush to
+// zero).  Keeps the conversions off GB300's narrow FP64 pipe.
+__device__ __forceinline__ double f2d(float x) {
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t e = (u >> 23) & 0xffu;
+    const uint64_t sign = (uint64_t)(u >> 31) << 63;
+    const uint64_t ex = e == 0u ? 0ull : (e == 255u ? (0x7ffull << 52) : (uint64_t)(e + 896u) << 52);
+    const uint64_t man = e == 0u ? 0ull : (uint64_t)(u & 0x7fffffu) << 29;
+    return __longlong_as_double((long long)(sign | ex | man));
+}
+
+// unevaluated float pairs (hi + lo): error-free sum (Knuth), pair sum
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF two_sum(float a, float b) {
+    const float t = a + b;
+    const float bv = t - a;
+    return {t, (a - (t - bv)) + (b - bv)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const FF t = two_sum(a.hi, b.hi);
+    const float e = t.lo + (a.lo + b.lo);
+    const float h = t.hi + e;
+    return {h, e - (h - t.hi)};
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return {-a.hi, -a.lo}; }
+
 struct Kernel {
     const PassArgs& a;
     Ctl& c;
@@ -289,21 +325,6 @@ struct Kernel {
 
     __device__ uint32_t slot(int s) const { return tbase + (uint32_t)s * SLOT_COLS; }
     __device__ static int c0_of(int ch) { return ch * 16; }
-
-    // deterministic block reduction over all threads (op 0: sum, 1: max)
-    __device__ double block_reduce(double v, int op) {
-        c.red[threadIdx.x] = v;
-        __syncthreads();
-        for (int o = THREADS / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o)
-                c.red[threadIdx.x] = op ? fmax(c.red[threadIdx.x], c.red[threadIdx.x + o])
-                                        : c.red[threadIdx.x] + c.red[threadIdx.x + o];
-            __syncthreads();
-        }
-        const double r = c.red[0];
-        __syncthreads();
-        return r;
-    }
 
     // all threads: make generic smem writes and TMEM stores visible to the MMA
     __device__ void sync_for_mma() {
@@ -412,8 +433,8 @@ struct Kernel {
     }
 
     // largest k <= kmax with 4^k max_r sum_c |T[sl]_rc| <= 1 (block-uniform).
-    // Row sums in FP32; the factor 1 + 2^-16 covers their rounding, so the
-    // bound stays an upper bound.
+    // Row sums and their maximum in FP32; the factor 1 + 2^-16 covers the
+    // sums' rounding, so the bound stays an upper bound.
     __device__ int fewer_steps(int sl, int kmax) {
         float rs = 0.f;
         for (int ch = ch0; ch < ch1; ++ch) {
@@ -422,27 +443,37 @@ struct Kernel {
 #pragma unroll
             for (int j = 0; j < 16; ++j) rs += fabsf(v[j]);
         }
-        c.red[threadIdx.x] = (double)rs;
+        c.red[threadIdx.x] = rs;
         __syncthreads();
-        double tot = 0.0;
-        if (grp == 0)
-            for (int g = 0; g < GROUPS; ++g) tot += c.red[row + 128 * g];
+        if (grp == 0) {
+            float tot = c.red[row];
+            for (int g = 1; g < GROUPS; ++g) tot += c.red[row + 128 * g];
+            for (int o = 16; o > 0; o >>= 1) tot = fmaxf(tot, __shfl_down_sync(0xffffffffu, tot, o));
+            if ((threadIdx.x & 31) == 0) c.wred[threadIdx.x >> 5] = tot;
+        }
         __syncthreads();
-        const double qmax = block_reduce(tot * (double)TMEM_INV, 1) * (1.0 + 0x1p-16);
-        int k = 0;
-        while (k < kmax && qmax * ldexp(1.0, 2 * (k + 1)) <= 1.0) ++k;
-        return k;
+        if (threadIdx.x == 0) {
+            float q = c.wred[0];
+            for (int w = 1; w < 4; ++w) q = fmaxf(q, c.wred[w]);
+            const double qmax = (double)q * (double)TMEM_INV * (1.0 + 0x1p-16);
+            int k = 0;
+            while (k < kmax && qmax * ldexp(1.0, 2 * (k + 1)) <= 1.0) ++k;
+            c.kfew = k;
+        }
+        __syncthreads();
+        return c.kfew;
     }
 
     // Matrix times NC vectors on the CUDA cores: P_g[cc][row] = sum over this
     // column group's k of M_row,k v[k][cc], M = scale x TMEM slot sl.  v is in
     // shared memory as [k][NC + 4] floats (broadcast float4 reads); FP32
     // products are summed per 16-column chunk (round to nearest), the chunk
-    // sums without rounding error (float pairs, then FP64).  P holds the two groups' partials, [2][NC][NMAX] doubles
-    // (column-major, so the row-indexed stores are conflict-free); the caller
-    // adds P_0 + P_1 after a barrier.
+    // sums without rounding error (float pairs).  P holds the two groups'
+    // partials as float pairs, [2][NC][NMAX] (column-major, so the
+    // row-indexed stores are conflict-free); the caller adds P_0 + P_1 after a
+    // barrier.
     template <int NC>
-    __device__ void rowvec(int sl, float scale, const float* v, double* P) {
+    __device__ void rowvec(int sl, float scale, const float* v, FF* P) {
         constexpr int VL = NC + 4;
         float hi[NC], lo[NC];  // chunk sums accumulated as unevaluated float pairs
 #pragma unroll
@@ -468,16 +499,15 @@ struct Kernel {
                 }
             }
 #pragma unroll
-            for (int cc = 0; cc < NC; ++cc) {  // error-free sum (Knuth's TwoSum)
-                const float t = hi[cc] + acc[cc];
-                const float bv = t - hi[cc];
-                lo[cc] += (hi[cc] - (t - bv)) + (acc[cc] - bv);
-                hi[cc] = t;
+            for (int cc = 0; cc < NC; ++cc) {
+                const FF t = two_sum(hi[cc], acc[cc]);
+                hi[cc] = t.hi;
+                lo[cc] += t.lo;
             }
         }
-        double* Pg = P + grp * (NC * NMAX);
+        FF* Pg = P + grp * (NC * NMAX);
 #pragma unroll
-        for (int cc = 0; cc < NC; ++cc) Pg[cc * NMAX + row] = (double)hi[cc] + (double)lo[cc];
+        for (int cc = 0; cc < NC; ++cc) Pg[cc * NMAX + row] = two_sum(hi[cc], lo[cc]);
     }
 
     // row `row` of NC float vectors, [row][NC + 4] (16-byte stores, conflict-free)
@@ -492,18 +522,19 @@ struct Kernel {
     // The last doubling on the core columns, on CUDA cores: w = Z_s e_c =
     // 2 (I + Z^2)^-1 Z e_c by iterative refinement with the tensor-core
     // inverse X as preconditioner,  w <- w + X (2 z - w - Z (Z w)),  every
-    // product rounded to nearest.  The saturated occupations (and Tr_c d) then
-    // carry no accumulation bias.  Writes d = (I - Z_s)/2 on the core columns.
+    // product rounded to nearest and every sum carried as a float pair.  The
+    // saturated occupations (and Tr_c d) then carry no accumulation bias.
+    // Writes d = (I - Z_s)/2 on the core columns and its core diagonal terms.
     // Scratch: staged operands S0 and S1 (free at this point).  All threads.
     template <int NC>
-    __device__ void refine_core(int zs, int xs, float zsc, int ncore, double& tr_d) {
+    __device__ void refine_core(int zs, int xs, float zsc, int ncore) {
         constexpr int VL = NC + 4;
         float* Vz = (float*)st[0];
         float* Vw = Vz + NMAX * VL;
         float* Vt = Vw + NMAX * VL;
-        double* Wd = (double*)(Vt + NMAX * VL);  // [NC][NMAX]
-        double* P = Wd + NC * NMAX;              // [2][NC][NMAX]
-        const double* P1 = P + NC * NMAX;
+        FF* Wd = (FF*)(Vt + NMAX * VL);  // [NC][NMAX]
+        FF* P = Wd + NC * NMAX;          // [2][NC][NMAX]
+        const FF* P1 = P + NC * NMAX;
         const bool live = grp == 0 && row < n;
         for (int b0 = 0; b0 < ncore; b0 += NC) {
             const int nc = min(NC, ncore - b0);
@@ -521,9 +552,10 @@ struct Kernel {
             if (grp == 0) {
 #pragma unroll
                 for (int cc = 0; cc < NC; ++cc) {
-                    const double w0 = (live && cc < nc) ? 2.0 * (P[cc * NMAX + row] + P1[cc * NMAX + row]) : 0.0;
+                    FF w0 = ff_add(P[cc * NMAX + row], P1[cc * NMAX + row]);
+                    w0 = (live && cc < nc) ? FF{2.f * w0.hi, 2.f * w0.lo} : FF{0.f, 0.f};
                     Wd[cc * NMAX + row] = w0;
-                    x[cc] = (float)w0;
+                    x[cc] = w0.hi;
                 }
                 put_row<NC>(Vw, x);
             }
@@ -534,7 +566,7 @@ struct Kernel {
                 if (grp == 0) {
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc)
-                        x[cc] = live ? (float)(P[cc * NMAX + row] + P1[cc * NMAX + row]) : 0.f;
+                        x[cc] = live ? ff_add(P[cc * NMAX + row], P1[cc * NMAX + row]).hi : 0.f;
                     put_row<NC>(Vt, x);
                 }
                 __syncthreads();
@@ -543,9 +575,10 @@ struct Kernel {
                 if (grp == 0) {
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) {
-                        const double res = 2.0 * (double)Vz[row * VL + cc] - Wd[cc * NMAX + row] -
-                                           (P[cc * NMAX + row] + P1[cc * NMAX + row]);
-                        x[cc] = (live && cc < nc) ? (float)res : 0.f;
+                        const FF zz = ff_add(P[cc * NMAX + row], P1[cc * NMAX + row]);
+                        const FF res = ff_add(ff_add(FF{2.f * Vz[row * VL + cc], 0.f}, ff_neg(Wd[cc * NMAX + row])),
+                                              ff_neg(zz));
+                        x[cc] = (live && cc < nc) ? res.hi : 0.f;
                     }
                     put_row<NC>(Vt, x);
                 }
@@ -555,10 +588,10 @@ struct Kernel {
                 if (grp == 0) {
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) {
-                        double w = Wd[cc * NMAX + row];
-                        if (live && cc < nc) w += P[cc * NMAX + row] + P1[cc * NMAX + row];
+                        FF w = Wd[cc * NMAX + row];
+                        if (live && cc < nc) w = ff_add(w, ff_add(P[cc * NMAX + row], P1[cc * NMAX + row]));
                         Wd[cc * NMAX + row] = w;
-                        x[cc] = (float)w;
+                        x[cc] = w.hi;
                     }
                     put_row<NC>(Vw, x);
                 }
@@ -567,19 +600,25 @@ struct Kernel {
             if (live) {
                 for (int cc = 0; cc < nc; ++cc) {
                     const int kc = c.cpos[b0 + cc];
-                    const double dv = 0.5 * ((row == kc ? 1.0 : 0.0) - Wd[cc * NMAX + row]);
-                    if (!isfinite(dv)) set_error(a.err, GB_ERR_NAN);
-                    a.Dval[c.ocol[b0 + cc] + row] = dv;
-                    if (row == kc) tr_d += dv;
+                    // d = (delta - w) / 2 as a float pair (halving is exact)
+                    FF d = ff_add(FF{row == kc ? 1.f : 0.f, 0.f}, ff_neg(Wd[cc * NMAX + row]));
+                    d = FF{0.5f * d.hi, 0.5f * d.lo};
+                    if (!isfinite(d.hi)) set_error(a.err, GB_ERR_NAN);
+                    a.Dval[c.ocol[b0 + cc] + row] = f2d(d.hi) + f2d(d.lo);
+                    if (row == kc) {
+                        c.tv[T_DHI][b0 + cc] = d.hi;
+                        c.tv[T_DLO][b0 + cc] = d.lo;
+                    }
                 }
             }
             __syncthreads();
         }
     }
 
-    // core columns of slot sl (TMEM units) times `scale` into out[ocol + row];
-    // `tr` collects the core diagonal (times tscale).  Warps of column group 0.
-    __device__ void core_columns(int sl, int ncore, double scale, double* out, double tscale, double& tr) {
+    // core columns of slot sl (TMEM words) times k into out[ocol + row]; on
+    // the core diagonal the word times tk goes to trace term `term`.  Warps of
+    // column group 0.
+    __device__ void core_columns(int sl, int ncore, float k, double* out, int term, float tk) {
         if (grp != 0) return;
         for (int b0 = 0; b0 < ncore; b0 += 16) {
             const int nc = min(16, ncore - b0);
@@ -589,18 +628,18 @@ struct Kernel {
 #pragma unroll
                 for (int cc = 0; cc < 16; ++cc) {
                     if (cc < nc) {
-                        const double v = (double)g[cc] * (double)TMEM_INV;
-                        out[c.ocol[b0 + cc] + row] = scale * v;
-                        if (row == c.cpos[b0 + cc]) tr += tscale * v;
+                        out[c.ocol[b0 + cc] + row] = f2d(g[cc] * k);
+                        if (row == c.cpos[b0 + cc]) c.tv[term][b0 + cc] = g[cc] * tk;
                     }
                 }
             }
         }
     }
 
-    // element (row, row) of slot sl in values (warps of column group 0, rows < n)
-    __device__ double diag_elem(int sl) {
-        if (grp != 0) return 0.0;
+    // largest diagonal word of slot sl over rows < n into c.wred[0..3]
+    // (warps of column group 0; a barrier must follow before reading it)
+    __device__ void diag_max(int sl) {
+        if (grp != 0) return;
         const uint32_t cb = (uint32_t)(row & ~31);
         float u[16], w[16];
         tmem_ld16x2(slot(sl) + lane_off + cb, slot(sl) + lane_off + cb + 16, u, w);
@@ -611,7 +650,9 @@ struct Kernel {
             d = (j == q) ? u[q] : d;
             d = (j == q + 16) ? w[q] : d;
         }
-        return row < n ? (double)d * (double)TMEM_INV : 0.0;
+        d = row < n ? d : 0.f;
+        for (int o = 16; o > 0; o >>= 1) d = fmaxf(d, __shfl_down_sync(0xffffffffu, d, o));
+        if ((threadIdx.x & 31) == 0) c.wred[threadIdx.x >> 5] = d;
     }
 
     // pull the next subgraph's gathered blocks toward L2 while this one runs
@@ -645,12 +686,12 @@ struct Kernel {
     }
 
     // staged operand from a gathered block beta M (FP32, column groups of four):
-    // scale x blk, scale = 2^-(s+1) [x sigma] (exact power of two), and on the
-    // diagonal, when diag != nullptr, alpha (diag - shift) in FP64 rounded once
-    __device__ void stage_dense(const float* blk, float scale, const double* diag, double alpha, double shift, int sg) {
+    // scale x blk, scale = 2^-(s+1) [x sigma] (exact power of two), and, with
+    // use_diag, the diagonal dscale x c.dg (the x0 diagonal computed in FP64)
+    __device__ void stage_dense(const float* blk, float scale, bool use_diag, float dscale, int sg) {
         const float k = scale * STAGE_SCALE;
-        const bool has_diag = diag != nullptr && row < n;
-        const float dv = has_diag ? (float)(alpha * (diag[row] - shift)) * STAGE_SCALE : 0.f;
+        const bool has_diag = use_diag && row < n;
+        const float dv = has_diag ? c.dg[row] * dscale * STAGE_SCALE : 0.f;
         for (int ch = ch0; ch < ch1; ++ch) {
             const int c0 = c0_of(ch);
             float v[16];
@@ -714,15 +755,29 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
             c.ocol[e] = a.col_ptr[a.core_idx[c0 + e]];
         }
         K.prefetch_blocks(i + (int32_t)gridDim.x);
+        // the subgraph's scalars, once (FP64 is narrow on this part): step
+        // count s, and sigma_r = 2^-k with (beta / 2) sigma max row sum |h1_r| <= 1
+        if (threadIdx.x == 0) c.s = recursion_steps(a.beta, a.mu, a.eps_lo[i], a.eps_hi[i], a.min_steps);
+        if (threadIdx.x < a.m) {
+            const double h1max = a.h1max[(int64_t)i * a.m + threadIdx.x];
+            int k = 0;
+            double sig = 1.0;
+            while (0.5 * a.beta * sig * h1max > 1.0 && k < 100) {
+                sig *= 0.5;
+                ++k;
+            }
+            c.sigk[threadIdx.x] = k;
+        }
         __syncthreads();
-        int s = recursion_steps(a.beta, a.mu, a.eps_lo[i], a.eps_hi[i], a.min_steps);
-        double alpha = ldexp(a.beta, -(s + 1));
+        int s = c.s;
+        if (K.grp == 0)
+            c.dg[K.row] = K.row < n ? (float)(ldexp(a.beta, -(s + 1)) * (a.hdiag[s0 + K.row] - a.mu)) : 0.f;
+        __syncthreads();
         float* z1base = a.z1pool + (size_t)i * (a.m > 0 ? a.m : 1) * NMAX * NMAX;
 
         // ---- Taylor start: Q = x0^2, P = I - Q/3 + 2 Q^2/15 (slots: 0 Q, 1 P) ----
         const float* hb = a.hblk + a.boff[i];
-        const double* hd = a.hdiag + s0;
-        K.stage_dense(hb, ldexpf(1.f, -(s + 1)), hd, alpha, a.mu, 0);     // S0 = x0
+        K.stage_dense(hb, ldexpf(1.f, -(s + 1)), true, 1.f, 0);          // S0 = x0
         if (!K.gemm(0, 0, 0)) break;                                      // T0 = Q
         // rho(x0)^2 = rho(Q) <= max_r sum_c |Q_rc| (Gershgorin on the square is
         // tighter than on h): drop k steps while 2^k x0 keeps spectral radius <= 1
@@ -730,23 +785,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
         float qscale = 1.f;
         if (k > 0) {
             s -= k;
-            alpha = ldexp(a.beta, -(s + 1));
             qscale = ldexpf(1.f, 2 * k);
-            K.stage_dense(hb, ldexpf(1.f, -(s + 1)), hd, alpha, a.mu, 0); // S0 = 2^k x0
+            K.stage_dense(hb, ldexpf(1.f, -(s + 1)), true, ldexpf(1.f, k), 0);  // S0 = 2^k x0
         }
         K.combine(0, qscale, -1, 0.f, 0.f, -1, 1, nullptr);               // S1 = Q
         if (!K.gemm(1, 1, 1)) break;                                      // T1 = Q^2
         K.combine(0, -qscale / 3.f, 1, 2.f / 15.f, 1.f, 1, -1, nullptr);  // T1 = P
         bool ok = true;
         for (int r = 0; r < a.m && ok; ++r) {
-            // normalise the perturbation: (beta / 2) sigma max row sum |h1| <= 1
+            // the perturbation, normalised by sigma_r
             const float* h1b = a.hblk + (int64_t)(1 + r) * a.hblk_stride + a.boff[i];
-            const double h1max = a.h1max[(int64_t)i * a.m + r];
-            double sig = 1.0;
-            while (0.5 * a.beta * sig * h1max > 1.0 && sig > 1e-30) sig *= 0.5;
-            if (threadIdx.x == 0) c.sig[r] = sig;
+            const float x1scale = ldexpf(1.f, -(s + 1) - c.sigk[r]);
             // dZ0 = X1 P + x0 P1,  P1 = -Q1/3 + (2/15)(Q Q1 + Q1 Q),  Q1 = x0 X1 + X1 x0
-            K.stage_dense(h1b, (float)ldexp(sig, -(s + 1)), nullptr, 0.0, 0.0, 1);  // S1 = X1
+            K.stage_dense(h1b, x1scale, false, 0.f, 1);                     // S1 = X1
             K.sync_for_mma();
             if (threadIdx.x == 0) {
                 fence_after();
@@ -766,7 +817,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
             K.combine(2, -1.f / 3.f, 3, 2.f / 15.f, 0.f, -1, 1, nullptr);  // S1 = P1
             if (!(ok = K.gemm(2, 0, 1))) break;                            // T2 = x0 P1
             K.combine(1, 1.f, -1, 0.f, 0.f, -1, 2, nullptr);               // S2 = P
-            K.stage_dense(h1b, (float)ldexp(sig, -(s + 1)), nullptr, 0.0, 0.0, 1);  // S1 = X1
+            K.stage_dense(h1b, x1scale, false, 0.f, 1);                     // S1 = X1
             if (!(ok = K.gemm(2, 1, 2, 0, true))) break;                   // T2 += X1 P
             K.combine(2, 1.f, -1, 0.f, 0.f, -1, -1, z1base + (size_t)r * NMAX * NMAX);
         }
@@ -775,11 +826,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
         if (!K.gemm(2, 0, 2)) break;                                      // T2 = Z0 = x0 P
 
         // ---- doublings ----
-        double tr_l[GB_MAX_RHS];
-        for (int r = 0; r < a.m; ++r) tr_l[r] = 0.0;
         int zs = 2;
         float zscale = 1.f;
-        double tr_d = 0.0, tr_dd = 0.0, wmax = 0.0;
         for (int step = 0; step < s && ok; ++step) {
             int fr[3], q = 0;
             for (int k = 0; k < 4; ++k)
@@ -803,16 +851,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
             if (step == s - 1) {
                 // ---- the last doubling redone on the core columns (CUDA cores) ----
                 const float zsc = zscale * TMEM_INV;
-                if (ncore <= 8) K.refine_core<8>(zs, xs, zsc, ncore, tr_d);
-                else K.refine_core<16>(zs, xs, zsc, ncore, tr_d);
+                if (ncore <= 8) K.refine_core<8>(zs, xs, zsc, ncore);
+                else K.refine_core<16>(zs, xs, zsc, ncore);
                 // d (I - d) = (I - Z_s^2) / 4 = ((I - Y) X)^2 / 4: no cancellation
                 // near saturation (Y = Z_{s-1}^2, X = (I + Y)^-1)
                 K.combine(ys, -1.f, -1, 0.f, 1.f, -1, 1, nullptr);                      // S1 = I - Y
                 if (!(ok = K.gemm(zs, 1, 2))) break;                                    // G = (I - Y) X
                 K.combine(zs, 1.f, -1, 0.f, 0.f, -1, 1, nullptr);                       // S1 = G
                 if (!(ok = K.gemm(ys, 1, 1))) break;                                    // G^2
-                K.core_columns(ys, ncore, 0.25 * a.beta, a.d1mu_val, 0.25, tr_dd);     // d1_mu = beta G^2 / 4
-                wmax = 0.25 * a.beta * K.diag_elem(ys);
+                K.core_columns(ys, ncore, (float)(0.25 * a.beta) * TMEM_INV, a.d1mu_val, T_DD,
+                               0.25f * TMEM_INV);                                        // d1_mu = beta G^2 / 4
+                K.diag_max(ys);
             }
             if (a.m > 0) K.combine(ts, 2.f, -1, 0.f, 0.f, -1, 0, nullptr);              // S0 = W
             for (int r = 0; r < a.m && ok; ++r) {
@@ -832,8 +881,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
                 if (step < s - 1) {
                     K.combine(ys, 1.f, -1, 0.f, 0.f, -1, -1, z1);                       // Z1 -> global
                 } else {
-                    const double sc = -0.5 / c.sig[r];                                  // d1_lambda = -Z1_s / (2 sigma)
-                    K.core_columns(ys, ncore, sc, a.D1val[r], sc, tr_l[r]);
+                    const float sc = -ldexpf(0.5f, c.sigk[r]) * TMEM_INV;               // d1_lambda = -Z1_s / (2 sigma)
+                    K.core_columns(ys, ncore, sc, a.D1val[r], T_L0 + r, sc);
                 }
             }
             zs = ts;
@@ -841,28 +890,25 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
         }
         if (!ok) break;
 
-        // per-subgraph core traces: warp shuffles, then the warps' partials in a
-        // fixed order (deterministic)
-        const int nslot = TR_FIXED + a.m;
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        for (int sl = 0; sl < nslot; ++sl) {
-            double v = sl == TR_D ? tr_d : sl == TR_DD ? tr_dd : sl == TR_D1MU ? a.beta * tr_dd
-                     : sl == TR_FLOPS ? (threadIdx.x == 0 ? pass_gemm_flops(n, s, a.ns_iters, a.m) : 0.0)
-                     : sl == TR_MAXW ? wmax
-                                     : tr_l[sl - TR_D1LAM];
-            for (int o = 16; o > 0; o >>= 1) {
-                const double t = __shfl_down_sync(0xffffffffu, v, o);
-                v = sl == TR_MAXW ? fmax(v, t) : v + t;
-            }
-            if (lane == 0) c.red[sl * (THREADS / 32) + warp] = v;
-        }
+        // per-subgraph core traces: the core terms summed in FP64 in a fixed
+        // order (deterministic), one slot per thread
         __syncthreads();
-        if (threadIdx.x < nslot) {
+        if (threadIdx.x < TR_FIXED + a.m) {
             const int sl = threadIdx.x;
-            double v = c.red[sl * (THREADS / 32)];
-            for (int w = 1; w < THREADS / 32; ++w) {
-                const double t = c.red[sl * (THREADS / 32) + w];
-                v = sl == TR_MAXW ? fmax(v, t) : v + t;
+            double v = 0.0;
+            if (sl == TR_D) {
+                for (int e = 0; e < ncore; ++e) v += (double)c.tv[T_DHI][e] + (double)c.tv[T_DLO][e];
+            } else if (sl == TR_DD || sl == TR_D1MU) {
+                for (int e = 0; e < ncore; ++e) v += (double)c.tv[T_DD][e];
+                if (sl == TR_D1MU) v *= a.beta;
+            } else if (sl == TR_FLOPS) {
+                v = pass_gemm_flops(n, s, a.ns_iters, a.m);
+            } else if (sl == TR_MAXW) {
+                float g = c.wred[0];
+                for (int w = 1; w < 4; ++w) g = fmaxf(g, c.wred[w]);
+                v = 0.25 * a.beta * (double)g * (double)TMEM_INV;
+            } else {
+                for (int e = 0; e < ncore; ++e) v += (double)c.tv[T_L0 + sl - TR_D1LAM][e];
             }
             a.tr[(int64_t)i * a.tr_stride + sl] = v;
         }
