@@ -5,8 +5,9 @@
 //   A_hi B_hi + A_hi B_lo + A_lo B_hi,  x = hi + lo, hi = rn(x), lo = rn(x - hi)
 // with FP16 (default) or BF16 parts and FP32 accumulation in tensor memory.
 // Quantities that are close to the identity never pass through the 16-bit
-// parts: the Newton-Schulz residual R = I - X - Y X is accumulated onto a
-// TMEM copy of (I - X) and the correction X + X R onto the FP32 X itself.
+// parts: the Newton-Schulz residual R = (I - X) - Y X is formed in FP32 from
+// the FP32 X and the product (I - X exactly on the diagonal, where X is in
+// [1/2, 1]), and the correction X + X R accumulates onto the FP32 X itself.
 //
 // Scaling (powers of two, so exact): staged operands hold 2^12 x their value,
 // which keeps the FP16 lo parts of elements down to ~3e-5 out of the subnormal
@@ -24,7 +25,7 @@
 // The per-step schedule (Z FP32 in slot zs):
 //   stage Z -> S0;  Y = Z Z -> ys;  stage Y -> S1;  Y^2 -> ts;
 //   X0 = (98 I - 80 Y + 32 Y^2)/99 -> xs (FP32) and S2;
-//   repeat: (I - X) -> ts; ts += -Y X; stage R -> S0; xs += X R; stage X -> S2;
+//   repeat: Y X -> ts; stage R = (I - X) - Y X -> S0; xs += X R; stage X -> S2;
 //   stage Z -> S0; W/2 = X Z -> ts;
 //   per RHS: stage W -> S0, Z1 -> S1; X Z1 -> ys, W Z1 -> zs;
 //            Z1' = (2 X Z1) X - (W Z1 / 2) W -> ys -> global FP32
@@ -39,7 +40,7 @@
 
 namespace {
 
-constexpr int THREADS = 256;  // 8 warps: 4 TMEM lane quadrants x 2 column groups
+constexpr int THREADS = 384;  // 12 warps: 4 TMEM lane quadrants x 3 column groups
 constexpr int GROUPS = THREADS / 128;
 constexpr int NMAX = GB_SPLIT_MAX_N;
 constexpr int REFINE_ROUNDS = 1;  // refinement rounds of the final step (the tensor-core
@@ -159,6 +160,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
                  : "memory");
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// 16-column load without the wait (registers defined only after
+// tmem_wait_ld + pin16)
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// keeps every use of r behind the preceding wait
+__device__ __forceinline__ void pin16(uint32_t (&r)[16]) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) asm volatile("" : "+r"(r[j]));
 }
 
 // two 16-column loads (e.g. the same chunk of two slots) behind one wait
@@ -380,56 +399,64 @@ struct Kernel {
     }
 
     // Row-wise combination over this thread's 16-column chunks:
-    //   u = ca T[sA] + cb T[sB] + cd I   (cd on the diagonal of the n x n block)
+    //   u = (ca T[sA] + cd I) + cb T[sB]   (cd on the diagonal of the n x n block)
     // written to FP32 slot `out` (TMEM units), staged operand `sg` and/or the
     // global FP32 128 x 128 block `gdst` (values, in column groups of four:
     // element (r, c) at ((c / 4) * 128 + r) * 4 + c % 4); sB = -1 drops the
-    // second term.  Every
-    // slot is exactly zero outside the n x n block (the staged operands are),
-    // so only the identity needs masking.  The power-of-two unit changes are
-    // folded into the coefficients.
+    // second term.  Every slot is exactly zero outside the n x n block (the
+    // staged operands are), so only the identity needs masking.  The
+    // power-of-two unit changes are folded into the coefficients.
     __device__ void combine(int sA, float ca, int sB, float cb, float cd, int out, int sg, float* gdst) {
         const bool stage_only = out < 0 && gdst == nullptr;
         const float unit = stage_only ? STAGE_SCALE * TMEM_INV : 1.f;
         const float ka = ca * unit, kb = cb * unit, kd = cd * TMEM_SCALE * unit;
         const bool diag = cd != 0.f && row < n;
+        const bool two = sB >= 0;
+        const uint32_t ta = slot(sA) + lane_off, tb = slot(two ? sB : sA) + lane_off;
         for (int ch = ch0; ch < ch1; ++ch) {
-            const int c0 = ch * 16;
-            float u[16];
-            if (sB >= 0) {
-                float w[16];
-                tmem_ld16x2(slot(sA) + lane_off + c0, slot(sB) + lane_off + c0, u, w);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) u[j] = fmaf(kb, w[j], ka * u[j]);
-            } else {
-                tmem_ld16(slot(sA) + lane_off + c0, u);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) u[j] *= ka;
-            }
-            if (diag && (unsigned)(row - c0) < 16u) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (c0 + j == row) u[j] += kd;
-            }
-            if (out >= 0) tmem_st16(slot(out) + lane_off + c0, u);
-            if (sg >= 0) {
-                if (stage_only) {
-                    stage_chunk(st[sg], row, c0, u, fmt);
-                } else {
-                    float t[16];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) t[j] = u[j] * (STAGE_SCALE * TMEM_INV);
-                    stage_chunk(st[sg], row, c0, t, fmt);
-                }
-            }
-            if (gdst) {
-#pragma unroll
-                for (int j = 0; j < 16; j += 4)
-                    *(float4*)(gdst + ((size_t)((c0 + j) >> 2) * NMAX + row) * 4) =
-                        make_float4(u[j] * TMEM_INV, u[j + 1] * TMEM_INV, u[j + 2] * TMEM_INV, u[j + 3] * TMEM_INV);
-            }
+            uint32_t u[16], w[16];
+            tmem_ld16_issue(ta + 16 * ch, u);
+            if (two) tmem_ld16_issue(tb + 16 * ch, w);
+            tmem_wait_ld();
+            pin16(u);
+            if (two) pin16(w);
+            combine_chunk(16 * ch, u, w, two, ka, kb, kd, diag, out, sg, gdst, stage_only);
         }
         if (out >= 0) tmem_wait_st();
+    }
+
+    __device__ __forceinline__ void combine_chunk(int c0, const uint32_t (&ur)[16], const uint32_t (&wr)[16], bool two,
+                                                  float ka, float kb, float kd, bool diag, int out, int sg,
+                                                  float* gdst, bool stage_only) {
+        float u[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) u[j] = __uint_as_float(ur[j]) * ka;
+        if (diag && (unsigned)(row - c0) < 16u) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (c0 + j == row) u[j] += kd;
+        }
+        if (two) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) u[j] = fmaf(kb, __uint_as_float(wr[j]), u[j]);
+        }
+        if (out >= 0) tmem_st16(slot(out) + lane_off + c0, u);
+        if (sg >= 0) {
+            if (stage_only) {
+                stage_chunk(st[sg], row, c0, u, fmt);
+            } else {
+                float t[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) t[j] = u[j] * (STAGE_SCALE * TMEM_INV);
+                stage_chunk(st[sg], row, c0, t, fmt);
+            }
+        }
+        if (gdst) {
+#pragma unroll
+            for (int j = 0; j < 16; j += 4)
+                *(float4*)(gdst + ((size_t)((c0 + j) >> 2) * NMAX + row) * 4) =
+                    make_float4(u[j] * TMEM_INV, u[j + 1] * TMEM_INV, u[j + 2] * TMEM_INV, u[j + 3] * TMEM_INV);
+        }
     }
 
     // largest k <= kmax with 4^k max_r sum_c |T[sl]_rc| <= 1 (block-uniform).
@@ -468,9 +495,9 @@ struct Kernel {
     // column group's k of M_row,k v[k][cc], M = scale x TMEM slot sl.  v is in
     // shared memory as [k][NC + 4] floats (broadcast float4 reads); FP32
     // products are summed per 16-column chunk (round to nearest), the chunk
-    // sums without rounding error (float pairs).  P holds the two groups'
-    // partials as float pairs, [2][NC][NMAX] (column-major, so the
-    // row-indexed stores are conflict-free); the caller adds P_0 + P_1 after a
+    // sums without rounding error (float pairs).  P holds the column groups'
+    // partials as float pairs, [GROUPS][NC][NMAX] (column-major, so the
+    // row-indexed stores are conflict-free); the caller adds them after a
     // barrier.
     template <int NC>
     __device__ void rowvec(int sl, float scale, const float* v, FF* P) {
@@ -533,8 +560,14 @@ struct Kernel {
         float* Vw = Vz + NMAX * VL;
         float* Vt = Vw + NMAX * VL;
         FF* Wd = (FF*)(Vt + NMAX * VL);  // [NC][NMAX]
-        FF* P = Wd + NC * NMAX;          // [2][NC][NMAX]
-        const FF* P1 = P + NC * NMAX;
+        FF* P = Wd + NC * NMAX;          // [GROUPS][NC][NMAX]
+        // sum of the column groups' partials, in group order
+        auto psum = [&](int cc) {
+            FF t = P[cc * NMAX + row];
+#pragma unroll
+            for (int g = 1; g < GROUPS; ++g) t = ff_add(t, P[(g * NC + cc) * NMAX + row]);
+            return t;
+        };
         const bool live = grp == 0 && row < n;
         for (int b0 = 0; b0 < ncore; b0 += NC) {
             const int nc = min(NC, ncore - b0);
@@ -552,7 +585,7 @@ struct Kernel {
             if (grp == 0) {
 #pragma unroll
                 for (int cc = 0; cc < NC; ++cc) {
-                    FF w0 = ff_add(P[cc * NMAX + row], P1[cc * NMAX + row]);
+                    FF w0 = psum(cc);
                     w0 = (live && cc < nc) ? FF{2.f * w0.hi, 2.f * w0.lo} : FF{0.f, 0.f};
                     Wd[cc * NMAX + row] = w0;
                     x[cc] = w0.hi;
@@ -566,7 +599,7 @@ struct Kernel {
                 if (grp == 0) {
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc)
-                        x[cc] = live ? ff_add(P[cc * NMAX + row], P1[cc * NMAX + row]).hi : 0.f;
+                        x[cc] = live ? psum(cc).hi : 0.f;
                     put_row<NC>(Vt, x);
                 }
                 __syncthreads();
@@ -575,7 +608,7 @@ struct Kernel {
                 if (grp == 0) {
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) {
-                        const FF zz = ff_add(P[cc * NMAX + row], P1[cc * NMAX + row]);
+                        const FF zz = psum(cc);
                         const FF res = ff_add(ff_add(FF{2.f * Vz[row * VL + cc], 0.f}, ff_neg(Wd[cc * NMAX + row])),
                                               ff_neg(zz));
                         x[cc] = (live && cc < nc) ? res.hi : 0.f;
@@ -589,7 +622,7 @@ struct Kernel {
 #pragma unroll
                     for (int cc = 0; cc < NC; ++cc) {
                         FF w = Wd[cc * NMAX + row];
-                        if (live && cc < nc) w = ff_add(w, ff_add(P[cc * NMAX + row], P1[cc * NMAX + row]));
+                        if (live && cc < nc) w = ff_add(w, psum(cc));
                         Wd[cc * NMAX + row] = w;
                         x[cc] = w.hi;
                     }
@@ -839,9 +872,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
             if (!(ok = K.gemm(ts, 1, 1))) break;                                        // Y^2
             K.combine(ys, -80.f / 99.f, ts, 32.f / 99.f, 98.f / 99.f, xs, 2, nullptr);  // X0
             for (int j = 0; j < a.ns_iters && ok; ++j) {
-                K.combine(xs, -1.f, -1, 0.f, 1.f, ts, -1, nullptr);                     // I - X
-                if (!(ok = K.gemm(ts, 1, 2, 1, true))) break;                           // R = I - X - Y X
-                K.combine(ts, 1.f, -1, 0.f, 0.f, -1, 0, nullptr);                       // S0 = R
+                if (!(ok = K.gemm(ts, 1, 2))) break;                                    // T = Y X
+                K.combine(xs, -1.f, ts, -1.f, 1.f, -1, 0, nullptr);                     // S0 = R = (I - X) - Y X
                 if (!(ok = K.gemm(xs, 2, 0, 0, true))) break;                           // X += X R
                 K.combine(xs, 1.f, -1, 0.f, 0.f, -1, 2, nullptr);                       // S2 = X
             }
