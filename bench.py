@@ -1,16 +1,19 @@
 """Benchmark: orbitals/s for D + D1 on the 60,000-orbital water box.
 
-One step = the whole hot path on one synthetic system: graph_build (thresholded
-H) + partition (one water per core) + density_and_response (Fermi recursion,
-shared mu, canonical response with one H1, collect).  The split-precision
-tensor-core path (FP16 hi/lo parts, FP32 accumulation) is the headline; the
-plain FP64 GPU path is timed beside it on the same input.
+One step = the whole hot path on one synthetic system, second pass of the
+two-pass graph estimate: graph_build (|H| > tau joined with |D_1| > tau, D_1 =
+the density matrix of a first solve on the H graph, computed before timing) +
+partition (one water per core; a core whose subgraph would exceed 128
+orbitals is split into its atoms, then into orbitals) + density_and_response
+(Fermi recursion, shared mu, canonical response with one H1, collect).  The
+split-precision tensor-core path (FP16 hi/lo parts, FP32 accumulation) is the
+headline; the plain FP64 GPU path is timed beside it on the same graph.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 value  = orbitals / second with H, H1 resident in HBM (CUDA events, max over ranks)
 e2e    = the same through the public API from pinned host buffers: H2D of
-         H, H1 and D2H of D, D1, mu, mu1 inside the timed region
+         H, H1 and D2H of D, D1 inside the timed region
 L2 is flushed (512 MB write) before every timed step.
 """
 
@@ -32,7 +35,30 @@ sys.path.insert(0, ROOT)
 METRIC = "orbitals/s for D+D1 on 60k-orbital box, mixed vs FP64 path, max|ΔD|≤1e-5"
 WORKLOAD = "water10k"
 CONFIG_TEXT = ("10,000 H2O (60,000 orbitals), periodic box 66.9 A, sp tight binding, kT 0.2 eV, "
-               "graph = |H| > 1e-4, one molecule per core (10,000 subgraphs), one H1")
+               "two-pass graph |H| > 1e-4 or |D_1| > 1e-4 (D_1 from a first solve on the H graph), one "
+               "molecule per core (cores over 128 orbitals split into atoms), one H1")
+SUB_CAP = 128  # largest subgraph of the tensor-core kernel
+
+
+def rank_barrier(world, dist):
+    """All ranks meet before a timed step (no-op on one rank)."""
+    if world > 1:
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world, dist, device) -> float:
+    """The slowest rank's value: a timed region ends when every rank is done."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, ms: float, world: int) -> float:
+    """Units all ranks processed per second, timed by the slowest rank."""
+    return world * units_per_rank / (ms / 1e3)
 
 
 def parse():
@@ -58,10 +84,13 @@ def dist_env():
 def cpu_baseline(workload_name: str, budget_s: float = 15.0):
     """The oracle (graph method, per-subgraph LAPACK eigh) on a bounded sample.
 
-    Sample: the 1,000-water box from the same generator (same kT, tau and
-    subgraph shapes), repeated until about budget_s seconds have passed.
+    Sample: the 1,000-water box from the same generator (same kT and tau).  A
+    first, untimed solve on the H graph gives D_1; then second-pass steps
+    (graph from H and D_1, capped partition, solve) repeat until about
+    budget_s seconds have passed.
     """
     from oracle import graph_build as o_graph, oracle_graph, partition as o_part
+    from oracle.graph import partition_capped as o_part_capped
     from synth import WORKLOADS, make_workload
     from synth.workloads import Workload
 
@@ -70,20 +99,22 @@ def cpu_baseline(workload_name: str, budget_s: float = 15.0):
     _, system, h1 = make_workload(wl, n_rhs=1)
     H = system.H
     workers = os.cpu_count() or 1
+    adj = o_graph(H.n, H.indptr, H.indices, H.data, wl.tau)
+    d_1 = oracle_graph(H, h1, wl.kT, system.n_occ, o_part(adj, system.orb_group), workers=workers).D
     t0 = time.perf_counter()
     reps = 0
     while True:
-        adj = o_graph(H.n, H.indptr, H.indices, H.data, wl.tau)
-        part = o_part(adj, system.orb_group)
+        adj = o_graph(H.n, H.indptr, H.indices, H.data, wl.tau, d_prev=d_1)
+        part = o_part_capped(adj, system.orb_group, system.orb_atom, SUB_CAP)
         oracle_graph(H, h1, wl.kT, system.n_occ, part, workers=workers)
         reps += 1
         el = time.perf_counter() - t0
         if el > budget_s or reps >= 50:
             break
     return {"value": reps * H.n / el, "unit": "orbitals/s", "cores": workers, "kind": "oracle",
-            "sample": f"{reps} x oracle graph solve (graph, partition, eigh per subgraph, mu, mu1, collect) "
-                      f"of the 1,000-water box ({H.n} orbitals, kT {wl.kT}, tau {wl.tau}, m=1), "
-                      f"process pool of {workers}", "seconds": el}
+            "sample": f"{reps} x oracle second-pass step (graph from H and D_1, capped partition, eigh "
+                      f"per subgraph, mu, mu1, collect) of the 1,000-water box ({H.n} orbitals, kT {wl.kT}, "
+                      f"tau {wl.tau}, m=1), process pool of {workers}", "seconds": el}
 
 
 class ClockSampler:
@@ -151,34 +182,40 @@ def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world,
     H = gb.DeviceCSR.from_arrays(system.H.n, system.H.indptr, system.H.indices, system.H.data, dev)
     H1 = [gb.DeviceCSR.from_arrays(h.n, h.indptr, h.indices, h.data, dev) for h in h1]
     groups = torch.as_tensor(system.orb_group, device=dev)
+    atoms = torch.as_tensor(system.orb_atom, device=dev)
     n_groups = int(system.orb_group.max()) + 1
+    n_atoms = int(system.orb_atom.max()) + 1
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     launches = {"n": 0}
 
-    def step(precision, mu0, Hs=H, H1s=H1, max_newton=0):
-        G = gb.graph_build(Hs, wl.tau, handle=handle)
+    def step(precision, mu0, d_prev, Hs=H, H1s=H1, max_newton=0):
+        G = gb.graph_build(Hs, wl.tau, d_prev=d_prev, handle=handle)
         launches["n"] += handle.lib.gb_launch_count(handle.h)
-        P = gb.partition(G, groups, n_groups, handle=handle)
+        P = gb.partition(G, groups, n_groups, subgroups=atoms, n_subgroups=n_atoms, max_sub=SUB_CAP,
+                         handle=handle)
         launches["n"] += handle.lib.gb_launch_count(handle.h)
         R = gb.density_and_response(Hs, H1s, wl.kT, system.n_electrons, P, precision=precision, mu0=mu0,
                                     handle=handle, max_newton=max_newton, raise_on_error=max_newton == 0)
         launches["n"] += R.report["kernel_launches"]
         return P, R
 
-    def timed(precision, k, w, mu0):
+    def timed(precision, k, w, mu0, d_prev, adaptive=False):
+        """w untimed then k timed steps; the graph follows the previous D when adaptive."""
         for _ in range(w):
-            P, R = step(precision, mu0)
+            P, R = step(precision, mu0, d_prev)
             mu0 = R.mu
+            if adaptive:
+                d_prev = R.D
         times, kms, passes, flops = [], [], [], []
         launches["n"] = 0
+        last_input = d_prev
         for _ in range(k):
             flush.zero_()
             torch.cuda.synchronize(dev)
-            if world > 1:
-                dist.barrier()
+            rank_barrier(world, dist)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            P, R = step(precision, mu0)
+            P, R = step(precision, mu0, d_prev)
             e1.record(stream)
             torch.cuda.synchronize(dev)
             times.append(e0.elapsed_time(e1))
@@ -186,61 +223,75 @@ def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world,
             passes.append(R.report["passes"])
             flops.append(R.report["gemm_flops"])
             mu0 = R.mu
-        return P, R, times, kms, passes, flops, launches["n"]
+            last_input = d_prev
+            if adaptive:
+                d_prev = R.D
+        return P, R, times, kms, passes, flops, launches["n"], last_input
 
     out = {"workload": workload, "wl": wl, "system": system}
-    # split precision (FP16 parts): cold start for mu, then warm-started steps
-    _, R0, _, _, _, _, _ = timed("fp16x3", 0, max(warmup, 3), math.nan)
+    # split precision (FP16 parts): the first pass, a cold start on the H
+    # graph, gives D_1; then warm-started second-pass steps on the graph of
+    # H and D_1 (rebuilt every step)
+    _, R1, _, _, _, _, _, _ = timed("fp16x3", 0, 1, math.nan, None)
+    d_1 = R1.D
+    _, R0, _, _, _, _, _, _ = timed("fp16x3", 0, max(warmup, 3), R1.mu, d_1)
     clocks = ClockSampler(dev.index or 0)
     clocks.start()
-    P, Rm, t_m, k_m, pass_m, fl_m, n_launch = timed("fp16x3", steps, 0, R0.mu)
+    P, Rm, t_m, k_m, pass_m, fl_m, n_launch, dp = timed("fp16x3", steps, 0, R0.mu, d_1)
     out["clocks"] = clocks.stop()
-    t_step = statistics.mean(t_m)
-    if world > 1:
-        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
-    out.update(P=P, ms=t_step, value=world * system.n_orb / (t_step / 1e3), launches=n_launch,
+    t_step = max_over_ranks(statistics.mean(t_m), world, dist, dev)
+    sizes = (P.sub_ptr[1:] - P.sub_ptr[:-1]).float()
+    out.update(P=P, ms=t_step, value=whole_job_rate(system.n_orb, t_step, world), launches=n_launch,
                passes=pass_m[-1], max_steps=Rm.report["max_steps"], mu=Rm.mu, mu1=Rm.mu1[0],
                kernel_ms=statistics.mean(k / p for k, p in zip(k_m, pass_m)),
-               flops=statistics.mean(fl_m))
+               flops=statistics.mean(fl_m), mean_sub=float(sizes.mean().item()))
     Dm, D1m = Rm.D.val.clone(), Rm.D1[0].val.clone()
 
     if e2e_steps:
-        # public API from pinned host buffers: H2D of H, H1 and D2H of D, D1 inside the region
+        # public API from pinned host buffers: H2D of H, H1 and D2H of D, D1
+        # inside the region (D_1, the first pass's result, stays on the GPU)
         hp = [torch.as_tensor(a).pin_memory() for a in (system.H.indptr, system.H.indices.astype(np.int32),
                                                         system.H.data)]
         h1p = [torch.as_tensor(a).pin_memory() for a in (h1[0].indptr, h1[0].indices.astype(np.int32),
                                                          h1[0].data)]
-        host_out = [torch.empty(P.out_nnz, dtype=torch.float64).pin_memory() for _ in range(2)]
         bi = sum(t.numel() * t.element_size() for t in hp + h1p)
-        bo = 2 * P.out_nnz * 8
-        ts_e2e, mu_e = [], Rm.mu
+        cap = int(P.out_nnz * 1.25) + 4096
+        host_out = [torch.empty(cap, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+        ts_e2e, mu_e, bo = [], Rm.mu, 0
         for it in range(e2e_steps + 1):
             flush.zero_()
             torch.cuda.synchronize(dev)
+            rank_barrier(world, dist)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             Hd = gb.DeviceCSR(system.n_orb, *[t.to(dev, non_blocking=True) for t in hp])
             H1d = [gb.DeviceCSR(system.n_orb, *[t.to(dev, non_blocking=True) for t in h1p])]
-            _, Re = step("fp16x3", mu_e, Hs=Hd, H1s=H1d)
-            host_out[0].copy_(Re.D.val, non_blocking=True)
-            host_out[1].copy_(Re.D1[0].val, non_blocking=True)
+            Pe, Re = step("fp16x3", mu_e, d_1, Hs=Hd, H1s=H1d)
+            if Pe.out_nnz > cap:  # the graph grew past the buffers: grow them, drop this sample
+                cap = int(Pe.out_nnz * 1.25) + 4096
+                host_out = [torch.empty(cap, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+                it_valid = False
+            else:
+                it_valid = True
+            host_out[0][: Pe.out_nnz].copy_(Re.D.val, non_blocking=True)
+            host_out[1][: Pe.out_nnz].copy_(Re.D1[0].val, non_blocking=True)
             e1.record(stream)
             torch.cuda.synchronize(dev)
-            mu_e = Re.mu
-            if it > 0:
+            mu_e, bo = Re.mu, 2 * Pe.out_nnz * 8
+            if it > 0 and it_valid:
                 ts_e2e.append(e0.elapsed_time(e1))
-        ms_e2e = statistics.mean(ts_e2e)
-        out["e2e"] = {"value": world * system.n_orb / (ms_e2e / 1e3), "unit": "orbitals/s",
+        ms_e2e = max_over_ranks(statistics.mean(ts_e2e), world, dist, dev)
+        out["e2e"] = {"value": whole_job_rate(system.n_orb, ms_e2e, world), "unit": "orbitals/s",
                       "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": ms_e2e}
 
-    # the plain FP64 GPU path on the same input (its own mu), and both paths at one mu
-    _, R64, t64, k64, pass64, _, _ = timed("fp64", fp64_steps, 1, Rm.mu)
-    out["fp64"] = {"value": system.n_orb / (statistics.mean(t64) / 1e3), "unit": "orbitals/s",
-                   "ms_per_step": statistics.mean(t64), "passes": pass64[-1],
-                   "kernel_ms": statistics.mean(k64), "mu": R64.mu}
-    _, Rs = step("fp16x3", R64.mu, max_newton=1)
+    # the plain FP64 GPU path on the same graph and partition (same D_1), its
+    # own mu; then both paths at the FP64 mu
+    _, R64, t64, k64, pass64, _, _, _ = timed("fp64", fp64_steps, 1, Rm.mu, dp)
+    t64_ms = max_over_ranks(statistics.mean(t64), world, dist, dev)
+    out["fp64"] = {"value": whole_job_rate(system.n_orb, t64_ms, world) / world, "unit": "orbitals/s",
+                   "ms_per_step": t64_ms, "passes": pass64[-1], "kernel_ms": statistics.mean(k64),
+                   "mu": R64.mu}
+    _, Rs = step("fp16x3", R64.mu, dp, max_newton=1)
     out["accuracy_vs_fp64_gpu"] = {
         "max_abs_dD": float((Dm - R64.D.val).abs().max().item()),
         "max_abs_dD1": float((D1m - R64.D1[0].val).abs().max().item()),
@@ -305,10 +356,12 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f16x3-f32acc", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {workload_text(wl, system)}",
                        "n_orbitals": system.n_orb, "n_subgraphs": head["P"].n_sub,
-                       "max_subgraph": head["P"].max_sub, "m": 1, "kT": wl.kT, "tau": wl.tau,
+                       "max_subgraph": head["P"].max_sub, "mean_subgraph": round(head["mean_sub"], 1),
+                       "m": 1, "kT": wl.kT, "tau": wl.tau,
                        "l2": "flushed (512 MB write) before every timed step",
                        "parallelism": f"replicas x{world} (independent systems, no collective)",
-                       "step": "graph_build + partition + density_and_response (warm-started mu)"},
+                       "step": ("graph_build(H, D_1) + capped partition + density_and_response "
+                                "(warm-started mu); D_1 = first-pass density on the H graph")},
             "e2e": head.get("e2e"), "gpu_launches": head["launches"], "roofline": roof, "cpu_baseline": cpu,
             "clocks": head["clocks"], "fp64_path": head["fp64"],
             "mixed_over_fp64": head["value"] / world / head["fp64"]["value"],
@@ -331,8 +384,9 @@ def main():
 
 def workload_text(wl, system):
     return (f"{system.meta.get('n_waters')} H2O ({system.n_orb} orbitals), periodic box "
-            f"{system.box:.1f} A, sp tight binding, kT {wl.kT} eV, graph = |H| > {wl.tau:g}, one molecule "
-            f"per core, one H1")
+            f"{system.box:.1f} A, sp tight binding, kT {wl.kT} eV, two-pass graph |H| > {wl.tau:g} or "
+            f"|D_1| > {wl.tau:g} (D_1 from a first solve on the H graph), one molecule per core (cores "
+            f"over {SUB_CAP} orbitals split into atoms), one H1")
 
 
 def run_reference(args, rank, world):

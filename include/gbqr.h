@@ -201,6 +201,32 @@ size_t gb_partition_workspace_size(int32_t n, int64_t nnz_g, int32_t n_groups);
 int gb_partition(gb_handle* h, const gb_graph* G, const int32_t* group, int32_t n_groups,
                  int32_t target_core_size, gb_part* P);
 
+/* ---- gb_partition_capped ----------------------------------------------- *
+ * gb_partition with group ids, then a size cap on the subgraphs.  The paper
+ * leaves the choice of partition free (Sec. "Choosing the graph
+ * partitioning"); this rule keeps every subgraph within the tensor-core
+ * kernel's 128-row tile when the graph grows (e.g. built from D_prev):
+ *   1. cores = one per nonempty group id, as gb_partition (key g);
+ *   2. every core whose subgraph S_i holds more than max_sub vertices is
+ *      replaced by one core per distinct subgroup id among its vertices
+ *      (for example the atoms of a molecule; key n_groups + subgroup);
+ *   3. every replacement core still over max_sub is replaced by one core per
+ *      vertex (key n_groups + n_subgroups + v);
+ *   cores are ordered by ascending key, and halos and S_i follow as in
+ *   gb_partition.  A single-vertex core over max_sub is kept (P->max_sub
+ *   reports it).
+ *   subgroup  [device] int32[n], 0 <= subgroup[v] < n_subgroups; the vertices
+ *             of one subgroup should share one group id.
+ *   max_sub   cap on |S_i| (> 0).
+ * Other arguments, outputs and the capacity protocol are those of
+ * gb_partition (GB_ERR_CAPACITY reports the final sub_nnz).  Errors:
+ * GB_ERR_ARG (bad sizes, ids out of range, n_groups + n_subgroups + n over
+ * INT32_MAX).  Workspace: gb_partition_capped_workspace_size() (0 for
+ * invalid sizes).  Synchronises the stream. */
+size_t gb_partition_capped_workspace_size(int32_t n, int64_t nnz_g, int32_t n_groups, int32_t n_subgroups);
+int gb_partition_capped(gb_handle* h, const gb_graph* G, const int32_t* group, int32_t n_groups,
+                        const int32_t* subgroup, int32_t n_subgroups, int32_t max_sub, gb_part* P);
+
 /* ---- gb_partition_noalloc ---------------------------------------------- *
  * The same partition as gb_partition, for callers that cannot allocate device
  * memory: code running inside a host framework that owns every device

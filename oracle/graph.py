@@ -137,6 +137,32 @@ def partition(adj: Adjacency, groups=None, target_core_size: int = 6) -> Partiti
                      np.concatenate(core_pos).astype(np.int32))
 
 
+def partition_capped(adj: Adjacency, groups, subgroups, max_sub: int) -> Partition:
+    """Cores from group ids, with a cap on the subgraph size.
+
+    The paper leaves the partition free (Sec. "Choosing the graph
+    partitioning").  Rule: partition by group (key g); every core whose
+    subgraph holds more than ``max_sub`` vertices is replaced by one core per
+    subgroup id among its vertices (key G + subgroup, G above every group
+    id); every such core still over the cap is replaced by one core per
+    vertex (key G + S + v, S above every subgroup id).  Cores are ordered by
+    ascending key.
+    """
+    key = np.asarray(groups, dtype=np.int64)
+    sub = np.asarray(subgroups, dtype=np.int64)
+    n = adj.n
+    part = partition(adj, key)
+    for level, base in ((1, int(key.max()) + 1), (2, int(key.max()) + 1 + int(sub.max()) + 1)):
+        sizes = np.diff(part.sub_ptr)
+        big = {int(key[part.core_idx[part.core_ptr[k]]]) for k in np.nonzero(sizes > max_sub)[0]}
+        if not big:
+            break
+        piece = sub if level == 1 else np.arange(n)
+        key = np.array([base + piece[v] if int(key[v]) in big else key[v] for v in range(n)], dtype=np.int64)
+        part = partition(adj, key)
+    return part
+
+
 def gather(X, s: np.ndarray) -> np.ndarray:
     """Principal submatrix X[S, S] (X dense, or a scipy sparse matrix)."""
     if sp.issparse(X):

@@ -180,8 +180,13 @@ def graph_build(H: DeviceCSR, tau: float, *, paths2: bool = False, d_prev: CSC |
 
 
 def partition(G: Graph, groups: torch.Tensor | None = None, n_groups: int | None = None, *,
-              target_core_size: int = 6, handle: Handle | None = None) -> Partition:
-    """gb_partition: disjoint cores (one per group id, or blocks) and distance-1 halos."""
+              target_core_size: int = 6, subgroups: torch.Tensor | None = None,
+              n_subgroups: int | None = None, max_sub: int = 0, handle: Handle | None = None) -> Partition:
+    """gb_partition: disjoint cores (one per group id, or blocks) and distance-1 halos.
+
+    With ``subgroups`` and ``max_sub`` (gb_partition_capped), cores whose
+    subgraph exceeds ``max_sub`` are replaced by their subgroups.
+    """
     hd = handle or _default_handle(G.ptr.device)
     lib = hd.lib
     n = G.n
@@ -190,7 +195,16 @@ def partition(G: Graph, groups: torch.Tensor | None = None, n_groups: int | None
         groups = groups.to(device=dev, dtype=torch.int32).contiguous()
         if n_groups is None:
             n_groups = int(groups.max().item()) + 1
-    hd.workspace(lib.gb_partition_workspace_size(n, G.nnz, int(n_groups or 0) if groups is not None else 0))
+    capped = subgroups is not None and max_sub > 0
+    if capped:
+        if groups is None:
+            raise ValueError("a capped partition needs group ids")
+        subgroups = subgroups.to(device=dev, dtype=torch.int32).contiguous()
+        if n_subgroups is None:
+            n_subgroups = int(subgroups.max().item()) + 1
+        hd.workspace(lib.gb_partition_capped_workspace_size(n, G.nnz, int(n_groups), int(n_subgroups)))
+    else:
+        hd.workspace(lib.gb_partition_workspace_size(n, G.nnz, int(n_groups or 0) if groups is not None else 0))
     core_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
     core_idx = torch.empty(n, dtype=torch.int32, device=dev)
     core_pos = torch.empty(n, dtype=torch.int32, device=dev)
@@ -201,12 +215,16 @@ def partition(G: Graph, groups: torch.Tensor | None = None, n_groups: int | None
         sub_idx = torch.empty(cap, dtype=torch.int32, device=dev)
         p = L.gb_part(n, 0, 0, 0, 0, 0, cap, core_ptr.data_ptr(), core_idx.data_ptr(),
                       core_pos.data_ptr(), sub_ptr.data_ptr(), sub_idx.data_ptr())
-        st = lib.gb_partition(hd.h, C.byref(gs), None if groups is None else groups.data_ptr(),
-                              int(n_groups or 0), int(target_core_size), C.byref(p))
+        if capped:
+            st = lib.gb_partition_capped(hd.h, C.byref(gs), groups.data_ptr(), int(n_groups), subgroups.data_ptr(),
+                                         int(n_subgroups), int(max_sub), C.byref(p))
+        else:
+            st = lib.gb_partition(hd.h, C.byref(gs), None if groups is None else groups.data_ptr(),
+                                  int(n_groups or 0), int(target_core_size), C.byref(p))
         if st == 2:
             cap = int(p.sub_nnz) + 1
             continue
-        L.check("gb_partition", st)
+        L.check("gb_partition_capped" if capped else "gb_partition", st)
         return Partition(n, p.n_sub, p.max_sub, p.max_core, p.sub_nnz, p.out_nnz,
                          core_ptr[: p.n_sub + 1], core_idx, core_pos, sub_ptr[: p.n_sub + 1],
                          sub_idx[: p.sub_nnz])

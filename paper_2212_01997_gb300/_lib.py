@@ -74,6 +74,9 @@ SIGNATURES = [
     ("gb_partition_workspace_size", C.c_size_t, [C.c_int32, C.c_int64, C.c_int32]),
     ("gb_partition", C.c_int, [C.c_void_p, C.POINTER(gb_graph), C.c_void_p, C.c_int32, C.c_int32,
                                C.POINTER(gb_part)]),
+    ("gb_partition_capped_workspace_size", C.c_size_t, [C.c_int32, C.c_int64, C.c_int32, C.c_int32]),
+    ("gb_partition_capped", C.c_int, [C.c_void_p, C.POINTER(gb_graph), C.c_void_p, C.c_int32, C.c_void_p,
+                                      C.c_int32, C.c_int32, C.POINTER(gb_part)]),
     ("gb_partition_noalloc_scratch_bytes", C.c_size_t, []),
     ("gb_partition_noalloc", C.c_int, [C.c_void_p, C.POINTER(gb_graph), C.c_void_p, C.c_int32, C.c_int32,
                                        C.POINTER(gb_part)]),

@@ -217,6 +217,140 @@ extern "C" int gb_partition(gb_handle* h, const gb_graph* G, const int32_t* grou
 }
 
 // ---------------------------------------------------------------------------
+// gb_partition_capped: gb_partition, then cores whose subgraph exceeds max_sub
+// are replaced by their subgroups (see include/gbqr.h).
+// ---------------------------------------------------------------------------
+namespace {
+
+// flag the key of every core whose subgraph is larger than max_sub
+__global__ void k_mark_split(int32_t n_sub, const int64_t* sub_ptr, const int64_t* core_ptr,
+                             const int32_t* core_idx, const int32_t* key, int32_t max_sub, int32_t* split,
+                             int* any) {
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_sub) return;
+    if (sub_ptr[k + 1] - sub_ptr[k] > max_sub) {
+        split[key[core_idx[core_ptr[k]]]] = 1;
+        atomicExch(any, 1);
+    }
+}
+
+// new key of vertex v: base + (subgroup[v], or v itself) where its key was split
+__global__ void k_regroup(int32_t n, const int32_t* key, const int32_t* subgroup, int32_t n_subgroups,
+                          int32_t base, const int32_t* split, int32_t* newkey, int* err) {
+    const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int32_t part = v;
+    if (subgroup) {
+        part = subgroup[v];
+        if (part < 0 || part >= n_subgroups) {
+            set_error(err, GB_ERR_ARG);
+            part = 0;
+        }
+    }
+    newkey[v] = split[key[v]] ? base + part : key[v];
+}
+
+struct CapLayout {
+    int32_t* split;  // n_groups + n_subgroups
+    int32_t* key1;   // n
+    int32_t* key2;   // n
+    int* flags;      // 8
+};
+
+int64_t cap_keys(int32_t n, int32_t n_groups, int32_t n_subgroups) {
+    return (int64_t)n_groups + n_subgroups + n;
+}
+
+CapLayout layout_cap(Arena& a, int32_t n, int32_t n_groups, int32_t n_subgroups) {
+    CapLayout L;
+    L.split = a.take<int32_t>((size_t)n_groups + n_subgroups);
+    L.key1 = a.take<int32_t>(n);
+    L.key2 = a.take<int32_t>(n);
+    L.flags = a.take<int>(8);
+    return L;
+}
+
+// one refinement level: flag oversize cores of the partition keyed by `key`,
+// rekey their vertices; returns GB_OK with *more = 0 when nothing was split
+int cap_level(gb_handle* h, const gb_part* P, const int32_t* key, int32_t n_keys, const int32_t* subgroup,
+              int32_t n_subgroups, int32_t max_sub, const CapLayout& L, int32_t* newkey, int64_t* launches,
+              int* more) {
+    cudaStream_t s = h->stream;
+    const int32_t n = P->n;
+    const int tb = 256;
+    GB_CUDA(cudaMemsetAsync(L.split, 0, sizeof(int32_t) * n_keys, s));
+    GB_CUDA(cudaMemsetAsync(L.flags, 0, sizeof(int) * 8, s));
+    if (P->n_sub > 0) {
+        GB_LAUNCH(h, k_mark_split, (P->n_sub + tb - 1) / tb, tb, 0, P->n_sub, (const int64_t*)P->sub_ptr,
+                  (const int64_t*)P->core_ptr, (const int32_t*)P->core_idx, key, max_sub, L.split, L.flags);
+        ++*launches;
+    }
+    int any = 0;
+    GB_TRY(read_i32(h, L.flags, &any, 1));
+    *more = any;
+    if (!any) return GB_OK;
+    GB_LAUNCH(h, k_regroup, (n + tb - 1) / tb, tb, 0, n, key, subgroup, n_subgroups, n_keys,
+              (const int32_t*)L.split, newkey, L.flags + 1);
+    ++*launches;
+    int err = 0;
+    GB_TRY(read_i32(h, L.flags + 1, &err, 1));
+    return err;
+}
+
+}  // namespace
+
+extern "C" size_t gb_partition_capped_workspace_size(int32_t n, int64_t nnz_g, int32_t n_groups,
+                                                      int32_t n_subgroups) {
+    if (n <= 0 || n_groups <= 0 || n_subgroups <= 0 || cap_keys(n, n_groups, n_subgroups) > INT32_MAX) return 0;
+    Arena a;
+    a.off = gb_partition_workspace_size(n, nnz_g, (int32_t)cap_keys(n, n_groups, n_subgroups));
+    layout_cap(a, n, n_groups, n_subgroups);
+    return a.used();
+}
+
+extern "C" int gb_partition_capped(gb_handle* h, const gb_graph* G, const int32_t* group, int32_t n_groups,
+                                   const int32_t* subgroup, int32_t n_subgroups, int32_t max_sub, gb_part* P) {
+    if (!h || !G || !P || !group || !subgroup || n_groups <= 0 || n_subgroups <= 0 || max_sub <= 0)
+        return GB_ERR_ARG;
+    const int32_t n = G->n;
+    if (n <= 0 || cap_keys(n, n_groups, n_subgroups) > INT32_MAX) return GB_ERR_ARG;
+    // the inner partitions use the front of the workspace, this call's own
+    // arrays follow them
+    Arena a(h->ws, h->ws_bytes);
+    a.off = gb_partition_workspace_size(n, G->nnz, (int32_t)cap_keys(n, n_groups, n_subgroups));
+    CapLayout L = layout_cap(a, n, n_groups, n_subgroups);
+    if (!h->ws || !a.fits()) {
+        h->required_ws = gb_partition_capped_workspace_size(n, G->nnz, n_groups, n_subgroups);
+        return GB_ERR_WORKSPACE;
+    }
+    int64_t launches = 0;
+    // level 0: one core per group
+    int st = gb_partition(h, G, group, n_groups, 0, P);
+    launches += h->launches;
+    if (st != GB_OK && st != GB_ERR_CAPACITY) return st;
+    // level 1: oversize group cores -> one core per subgroup
+    int more = 0;
+    GB_TRY(cap_level(h, P, group, n_groups, subgroup, n_subgroups, max_sub, L, L.key1, &launches, &more));
+    if (!more) {
+        h->launches = launches;
+        return st;
+    }
+    const int32_t n_keys1 = n_groups + n_subgroups;
+    st = gb_partition(h, G, L.key1, n_keys1, 0, P);
+    launches += h->launches;
+    if (st != GB_OK && st != GB_ERR_CAPACITY) return st;
+    // level 2: oversize subgroup cores -> one core per vertex
+    GB_TRY(cap_level(h, P, L.key1, n_keys1, nullptr, 0, max_sub, L, L.key2, &launches, &more));
+    if (!more) {
+        h->launches = launches;
+        return st;
+    }
+    st = gb_partition(h, G, L.key2, n_keys1 + n, 0, P);
+    h->launches += launches;
+    return st;
+}
+
+// ---------------------------------------------------------------------------
 // gb_partition_noalloc: gb_partition for callers that cannot allocate device
 // memory (see include/gbqr.h).  Its scratch is a fixed file-scope device array
 // instead of the handle's workspace; it mirrors gb_partition step by step.

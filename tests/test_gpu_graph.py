@@ -5,6 +5,7 @@ import pytest
 import torch
 
 from oracle import graph_build as o_graph, oracle_graph, partition as o_part
+from oracle.graph import partition_capped as o_part_capped
 from synth import CSR, make_workload
 from tests.helpers import to_device
 
@@ -67,6 +68,41 @@ def test_graph_with_previous_density(gb):
         _check_graph(G, adj)
         P = gb.partition(G, torch.as_tensor(system.orb_group))
         _check_partition(P, o_part(adj, system.orb_group))
+
+
+def test_capped_partition_bit_exact(gb):
+    # adaptive graph of the 1,000-water box (|D_prev| > 1e-6 joins the H graph):
+    # a few one-molecule subgraphs exceed 128 orbitals and split into atoms
+    wl, system, _ = make_workload("water1k", n_rhs=0)
+    H = system.H
+    adj0 = o_graph(H.n, H.indptr, H.indices, H.data, 1e-4)
+    ref = oracle_graph(H, [], 0.2, system.n_occ, o_part(adj0, system.orb_group), workers=4)
+    col_ptr, row_idx, val = ref.D
+    dprev = gb.CSC(H.n, torch.as_tensor(col_ptr).cuda(), torch.as_tensor(row_idx, dtype=torch.int32).cuda(),
+                   torch.as_tensor(val).cuda())
+    G = gb.graph_build(to_device(H), 1e-6, d_prev=dprev)
+    adj = o_graph(H.n, H.indptr, H.indices, H.data, 1e-6, d_prev=(col_ptr, row_idx, val))
+    _check_graph(G, adj)
+    groups = torch.as_tensor(system.orb_group)
+    atoms = torch.as_tensor(system.orb_atom)
+    assert gb.partition(G, groups).max_sub > 128
+    P = gb.partition(G, groups, subgroups=atoms, max_sub=128)
+    part = o_part_capped(adj, system.orb_group, system.orb_atom, 128)
+    _check_partition(P, part)
+    assert P.max_sub <= 128 and part.n_sub > int(system.orb_group.max()) + 1
+    # random graph, tight cap: many groups split
+    rng = np.random.default_rng(8)
+    n = 257
+    A = rng.normal(size=(n, n)) * (rng.random((n, n)) < 0.03)
+    A = 0.5 * (A + A.T) + np.diag(rng.normal(size=n))
+    Ac = CSR.from_dense(A)
+    G = gb.graph_build(to_device(Ac), 0.0)
+    adj = o_graph(n, Ac.indptr, Ac.indices, Ac.data, 0.0)
+    grp = rng.integers(0, 40, size=n).astype(np.int32)
+    sub = (grp * 3 + rng.integers(0, 3, size=n)).astype(np.int32)
+    for cap in (12, 20, 30, 1000):
+        P = gb.partition(G, torch.as_tensor(grp), 40, subgroups=torch.as_tensor(sub), n_subgroups=120, max_sub=cap)
+        _check_partition(P, o_part_capped(adj, grp, sub, cap))
 
 
 def test_random_graph_blocks_and_edge_cases(gb):

@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 from oracle.graph import (collect_columns, column_mask, csc_to_dense, dense_polynomial, gather,
-                          graph_build, partition, polynomial_on_graph)
+                          graph_build, partition, partition_capped, polynomial_on_graph)
 from synth import CSR, make_workload
 
 
@@ -100,6 +100,53 @@ def test_partition_matches_brute_force():
     # no groups: consecutive blocks
     p2 = partition(adj, None, target_core_size=7)
     assert p2.n_sub == 8 and np.array_equal(p2.core(7), np.arange(49, 50))
+
+
+def test_partition_capped_rule_by_brute_force():
+    # cores whose subgraph exceeds the cap are replaced by their subgroups,
+    # and subgroup cores still over the cap by single vertices; order: kept
+    # groups, then kept subgroup cores, then vertex cores, each ascending
+    rng = np.random.default_rng(33)
+    n = 60
+    A = _random_sparse_sym(rng, n, 0.04)
+    Ac = CSR.from_dense(A)
+    adj = graph_build(n, Ac.indptr, Ac.indices, Ac.data, 0.0)
+    E = adj.to_dense()
+    groups = rng.integers(0, 9, size=n).astype(np.int32)
+    # subgroups: pairs of consecutive vertices, never crossing a group
+    subgroups = np.array([200 * groups[v] + v // 2 for v in range(n)], dtype=np.int32)
+
+    def nbhd(core):
+        return np.union1d(core, np.nonzero(E[core].any(axis=0))[0])
+
+    gsizes = {g: len(nbhd(np.nonzero(groups == g)[0])) for g in sorted(set(groups.tolist()))}
+    levels_seen = set()
+    for cap in sorted(set(gsizes.values()))[:-1] + [3]:
+        kept, subs, verts = [], [], []
+        for g in sorted(gsizes):
+            core = np.nonzero(groups == g)[0]
+            if len(nbhd(core)) <= cap:
+                kept.append(core)
+                continue
+            for sg in sorted(set(subgroups[core].tolist())):
+                sc = np.nonzero(subgroups == sg)[0]
+                if len(nbhd(sc)) <= cap:
+                    subs.append(sc)
+                else:
+                    verts.extend(np.array([v]) for v in sc)
+        verts.sort(key=lambda c: int(c[0]))
+        expected = kept + subs + verts
+        levels_seen.update(k for k, lst in enumerate((kept, subs, verts)) if lst)
+        part = partition_capped(adj, groups, subgroups, cap)
+        assert part.n_sub == len(expected)
+        for i, core in enumerate(expected):
+            assert np.array_equal(part.core(i), core)
+            assert np.array_equal(part.sub(i), nbhd(core))
+    assert levels_seen == {0, 1, 2}
+    # a cap above every subgraph leaves the partition unchanged
+    same = partition_capped(adj, groups, subgroups, max(gsizes.values()))
+    ref = partition(adj, groups)
+    assert np.array_equal(same.sub_idx, ref.sub_idx) and np.array_equal(same.core_idx, ref.core_idx)
 
 
 def test_sub_f_single_vertex_cores():
