@@ -13,7 +13,7 @@ import pytest
 import torch
 
 from oracle import graph_build as o_graph, oracle_graph, partition as o_part
-from oracle.graph import Partition as OPart
+from oracle.graph import Partition as OPart, partition_capped as o_part_capped
 from synth import CSR, make_workload
 from tests.helpers import dense_result, max_abs_block_error, to_device
 
@@ -107,13 +107,14 @@ def test_split_parity_at_fixed_mu(gb, name, kT, precision):
 
 
 def test_multiple_rhs_and_zero_rhs(gb):
-    wl, system, h1, kT, part, Hd, H1d, P = _setup(gb, "water64", n_rhs=3)
+    # m = 6 right-hand sides per subgraph in one launch (the Krylov rank-m update)
+    wl, system, h1, kT, part, Hd, H1d, P = _setup(gb, "water64", n_rhs=6)
     ref = oracle_graph(system.H, h1, kT, system.n_occ, part)
     for prec in ("fp64", "fp16x3"):
         R = gb.density_and_response(Hd, H1d, kT, system.n_electrons, P, precision=prec, mu0=ref.mu)
         eD, eD1 = max_abs_block_error(R, ref, part)
         assert eD <= TOL[prec] and eD1 <= TOL[prec]
-        for r in range(3):
+        for r in range(6):
             assert abs(R.mu1[r] - ref.mu1[r]) < (1e-8 if prec == "fp64" else 1e-3) * max(1, abs(ref.mu1[r]))
         R0 = gb.density_and_response(Hd, [], kT, system.n_electrons, P, precision=prec, mu0=ref.mu)
         assert np.abs(dense_result(R0.D) - dense_result(R.D)).max() < TOL[prec]
@@ -153,6 +154,55 @@ def test_ragged_random_subgraphs(gb, precision):
     print(f"random {precision}: sizes {sizes.min()}..{sizes.max()} max|dD|={eD:.2e} max|dD1|={eD1:.2e}")
     assert eD <= TOL[precision] and eD1 <= TOL[precision]
     assert abs(R.mu - ref.mu) < (1e-9 if precision == "fp64" else 1e-4)
+
+
+def test_fp64_paths_of_two_large_subgraphs(gb):
+    # graph squared (paths of length two): subgraphs of 256-313 orbitals on the
+    # FP64 path; the split path refuses them (above its 128-row tile)
+    wl, system, h1 = make_workload("water64", n_rhs=1)
+    H = system.H
+    adj = o_graph(H.n, H.indptr, H.indices, H.data, wl.tau, paths2=True)
+    part = o_part(adj, system.orb_group)
+    assert part.sizes().min() > 200
+    ref = oracle_graph(H, h1, wl.kT, system.n_occ, part)
+    Hd = to_device(H)
+    P = gb.partition(gb.graph_build(Hd, wl.tau, paths2=True), torch.as_tensor(system.orb_group))
+    R = gb.density_and_response(Hd, [to_device(h1[0])], wl.kT, system.n_electrons, P, precision="fp64")
+    eD, eD1 = max_abs_block_error(R, ref, part)
+    assert eD <= TOL["fp64"] and eD1 <= TOL["fp64"]
+    # mu is pinned through the electron count (a gapped box leaves it loosely
+    # determined); Tr D1 = 0 keeps the count under the perturbation
+    assert abs(R.report["occ_residual"]) <= 1e-10 * system.n_occ
+    assert abs(np.trace(dense_result(R.D, R.D1[0].val))) < 1e-9
+    bad = gb.density_and_response(Hd, [to_device(h1[0])], wl.kT, system.n_electrons, P, precision="fp16x3",
+                                  raise_on_error=False)
+    assert bad.status == 8  # GB_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp16x3"])
+def test_two_pass_graph_capped_partition(gb, precision):
+    # second pass of the two-pass graph estimate on the 1,000-water box:
+    # |D_1| > 1e-6 joins the H graph, D_1 from the oracle on the H graph; a few
+    # one-molecule subgraphs exceed 128 and split into atoms
+    wl, system, h1 = make_workload("water1k", n_rhs=1)
+    H = system.H
+    kT, tau = 0.2, 1e-6
+    adj0 = o_graph(H.n, H.indptr, H.indices, H.data, wl.tau)
+    d_1 = oracle_graph(H, [], kT, system.n_occ, o_part(adj0, system.orb_group), workers=4).D
+    adj = o_graph(H.n, H.indptr, H.indices, H.data, tau, d_prev=d_1)
+    part = o_part_capped(adj, system.orb_group, system.orb_atom, 128)
+    assert part.sizes().max() <= 128 and part.n_sub > 1000
+    ref = oracle_graph(H, h1, kT, system.n_occ, part, workers=4)
+    Hd = to_device(H)
+    dprev = gb.CSC(H.n, torch.as_tensor(d_1[0]).cuda(), torch.as_tensor(d_1[1], dtype=torch.int32).cuda(),
+                   torch.as_tensor(d_1[2]).cuda())
+    G = gb.graph_build(Hd, tau, d_prev=dprev)
+    P = gb.partition(G, torch.as_tensor(system.orb_group), subgroups=torch.as_tensor(system.orb_atom),
+                     max_sub=128)
+    R = gb.density_and_response(Hd, [to_device(h1[0])], kT, system.n_electrons, P, precision=precision)
+    eD, eD1 = max_abs_block_error(R, ref, part)
+    print(f"two-pass {precision}: n_sub {P.n_sub} max|dD|={eD:.2e} max|dD1|={eD1:.2e} dmu={R.mu - ref.mu:.2e}")
+    assert eD <= TOL[precision] and eD1 <= TOL[precision]
 
 
 def test_single_subgraph_equals_full(gb):
