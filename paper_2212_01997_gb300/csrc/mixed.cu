@@ -1,13 +1,17 @@
 // Split-precision Fermi / response recursion on the 5th-generation tensor
 // cores (tcgen05), one subgraph (|S_i| <= 128) per CTA.
 //
-// Every matrix product A B runs as three tcgen05.mma (kind::f16) passes
-//   A_hi B_hi + A_hi B_lo + A_lo B_hi,  x = hi + lo, hi = rn(x), lo = rn(x - hi)
-// with FP16 (default) or BF16 parts and FP32 accumulation in tensor memory.
-// Quantities that are close to the identity never pass through the 16-bit
-// parts: the Newton-Schulz residual R = (I - X) - Y X is formed in FP32 from
-// the FP32 X and the product (I - X exactly on the diagonal, where X is in
-// [1/2, 1]), and the correction X + X R accumulates onto the FP32 X itself.
+// Every matrix product A B is split into FP16 (default) or BF16 parts,
+// x = hi + lo, hi = rn(x), lo = rn(x - hi), and summed as
+//   A_hi B_hi + A_hi B_lo + A_lo B_hi
+// with FP32 accumulation in tensor memory.  An M = 128 tcgen05.mma costs the
+// same for any N <= 256, so A_hi B_hi and A_hi B_lo share one instruction of
+// N = 2 npad ([B_hi | B_lo] staged side by side): 2 K + 1 instructions per
+// product instead of 3 K.  The product P lands in two TMEM halves (left:
+// A_hi B_hi + A_lo B_hi, right: A_hi B_lo) that the staging pass adds.
+// Quantities close to the identity never pass through the 16-bit parts: the
+// Newton-Schulz residual R = (I - X) - Y X is formed in FP32 from the FP32 X
+// and the product (I - X exact on the diagonal, where X is in [1/2, 1]).
 //
 // Scaling (powers of two, so exact): staged operands hold 2^12 x their value,
 // which keeps the FP16 lo parts of elements down to ~3e-5 out of the subnormal
@@ -17,22 +21,22 @@
 // (the response is linear in h1; d1_lambda is unscaled by 1/sigma at the end),
 // which bounds every response matrix by O(1).
 //
-// Resources per CTA: TMEM 512 columns = four 128-column FP32 slots; shared
-// memory = three staged operands (128 rows x 128 K, hi + lo, 64 KB each) laid
-// out K-major in 8x8 core matrices without swizzle: element (r, k) at byte
-// (k/8)*2048 + (r/8)*128 + (r%8)*16 + (k%8)*2.
+// Resources per CTA: TMEM 512 columns holding Z and X (FP32, npad columns
+// each) and P (2 npad); shared memory = three staged operands (128 rows, hi
+// and lo parts, 64 KB each) laid out K-major in 8x8 core matrices without
+// swizzle: element (r, k) of the hi part at byte
+// (k/8)*2048 + (r/8)*128 + (r%8)*16 + (k%8)*2, the lo part npad*256 bytes on.
 //
-// The per-step schedule (Z FP32 in slot zs):
-//   stage Z -> S0;  Y = Z Z -> ys;  stage Y -> S1;  Y^2 -> ts;
-//   X0 = (98 I - 80 Y + 32 Y^2)/99 -> xs (FP32) and S2;
-//   repeat: Y X -> ts; stage R = (I - X) - Y X -> S0; xs += X R; stage X -> S2;
-//   stage Z -> S0; W/2 = X Z -> ts;
-//   per RHS: stage W -> S0, Z1 -> S1; X Z1 -> ys, W Z1 -> zs;
-//            Z1' = (2 X Z1) X - (W Z1 / 2) W -> ys -> global FP32
-//            (last step: only its core columns, as d1_lambda);
-//   new Z = 2 * ts.
-// The last step also redoes Z_s on the core columns on the CUDA cores (see
-// refine_core) and forms d1_mu = beta ((I - Y) X)^2 / 4.
+// The per-step schedule (Z FP32 in TMEM):
+//   stage Z -> S0;  P = Z Z;  stage Y -> S1;  P = Y Y (hi parts: it only seeds
+//   Newton-Schulz);  X0 = (98 I - 80 Y + 32 Y^2)/99 -> X and S2;
+//   repeat: P = Y X; stage R = (I - X) - P -> S0; P = X R; X += P -> X, S2;
+//   stage Z -> S0; P = W/2 = X Z; Z = 2 P (next step), stage W -> S0;
+//   per RHS: stage Z1 -> S1; P = X Z1 -> X region (x2); P = W Z1 -> S1 (x -1/2);
+//            P = (-W Z1 / 2) W; stage 2 X Z1 -> S1; P += (2 X Z1) X -> global FP32
+//            (last step: only its core columns, as d1_lambda).
+// The last step also forms d1_mu = beta ((I - Y) X)^2 / 4 and redoes Z_s on
+// the core columns on the CUDA cores (see refine_core).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -51,7 +55,6 @@ constexpr int NSTAGE = 3;
 constexpr uint32_t LBO = 128 * (NMAX / 8);         // next 8-column group (K direction)
 constexpr uint32_t SBO = 128;                      // next 8-row group (M/N direction)
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t SLOT_COLS = 128;
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 constexpr float STAGE_SCALE = 4096.f;               // staged operand = 2^12 x value
 constexpr float TMEM_SCALE = 16777216.f;            // TMEM word = 2^24 x value
@@ -266,7 +269,8 @@ __device__ __forceinline__ void split_pair(float x0, float x1, int fmt, uint32_t
 }
 
 // write 16 consecutive columns [c0, c0+16) of row r into a staged operand
-__device__ __forceinline__ void stage_chunk(uint8_t* stage, int r, int c0, const float* v, int fmt) {
+// (hi part at the layout offset, lo part lo_off bytes further)
+__device__ __forceinline__ void stage_chunk(uint8_t* stage, int r, int c0, const float* v, int fmt, uint32_t lo_off) {
     uint32_t hi[8], lo[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) split_pair(v[2 * j], v[2 * j + 1], fmt, hi[j], lo[j]);
@@ -274,8 +278,8 @@ __device__ __forceinline__ void stage_chunk(uint8_t* stage, int r, int c0, const
     uint8_t* p1 = stage + elem_off(r, c0 + 8);
     *(uint4*)p0 = make_uint4(hi[0], hi[1], hi[2], hi[3]);
     *(uint4*)p1 = make_uint4(hi[4], hi[5], hi[6], hi[7]);
-    *(uint4*)(p0 + HALF_BYTES) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-    *(uint4*)(p1 + HALF_BYTES) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+    *(uint4*)(p0 + lo_off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    *(uint4*)(p1 + lo_off) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
 }
 
 // float -> double by integer operations (exact; FP32 subnormals flush to
@@ -306,6 +310,14 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
 }
 __device__ __forceinline__ FF ff_neg(FF a) { return {-a.hi, -a.lo}; }
 
+enum SrcKind { SRC_NONE = 0, SRC_TMEM = 1, SRC_PAIR = 2, SRC_STAGED = 3 };
+struct Src {
+    int kind;
+    uint32_t c, c2;  // TMEM columns (SRC_TMEM; SRC_PAIR: left, right)
+    int stage;       // SRC_STAGED
+    float k;         // coefficient
+};
+
 struct Kernel {
     const PassArgs& a;
     Ctl& c;
@@ -320,6 +332,8 @@ struct Kernel {
     int grp;       // column group: chunks [ch0, ch1) of 16 columns
     int ch0, ch1;
     uint32_t lane_off;
+    uint32_t lo_off;          // bytes from a staged operand's hi part to its lo part (npad x 256)
+    uint32_t zc, xc, pl, pr;  // TMEM columns: Z, X (FP32 state), product left / right halves
 
     __device__ Kernel(const PassArgs& a_, Ctl& c_, uint8_t* smem) : a(a_), c(c_) {
         for (int k = 0; k < NSTAGE; ++k) {
@@ -334,16 +348,33 @@ struct Kernel {
         lane_off = (uint32_t)((row & ~31) << 16);
     }
 
+    // Per-subgraph layout.  Staged operand: hi part in 8-column groups 2048 B
+    // apart, lo part right after it (lo_off = npad/8 groups), so [B_hi | B_lo]
+    // read MN-major is one operand of N = 2 npad.  TMEM (4 npad <= 512
+    // columns): Z at 0, X at npad, the product P at 2 npad (left) and 3 npad
+    // (right half: the A_hi B_lo term of a packed product).
     __device__ void set_size(int n_) {
         n = n_;
         npad = (n + 15) & ~15;
         const int nch = npad / 16, per = (nch + GROUPS - 1) / GROUPS;
         ch0 = min(nch, grp * per);
         ch1 = min(nch, ch0 + per);
+        lo_off = (uint32_t)npad * 256u;
+        zc = 0;
+        xc = (uint32_t)npad;
+        pl = 2u * (uint32_t)npad;
+        pr = 3u * (uint32_t)npad;
     }
 
-    __device__ uint32_t slot(int s) const { return tbase + (uint32_t)s * SLOT_COLS; }
+    __device__ uint32_t col(uint32_t cidx) const { return tbase + cidx; }
     __device__ static int c0_of(int ch) { return ch * 16; }
+
+    // combine sources: a TMEM region, the packed product (left + right), a
+    // staged operand (hi + lo), each times a coefficient
+    __device__ Src T(uint32_t c_, float k) const { return {SRC_TMEM, c_, 0u, 0, k}; }
+    __device__ Src Pk(float k) const { return {SRC_PAIR, pl, pr, 0, k}; }
+    __device__ Src S(int stage, float k) const { return {SRC_STAGED, 0u, 0u, stage, k}; }
+    __device__ static Src none() { return {SRC_NONE, 0u, 0u, 0, 0.f}; }
 
     // all threads: make generic smem writes and TMEM stores visible to the MMA
     __device__ void sync_for_mma() {
@@ -352,26 +383,37 @@ struct Kernel {
         __syncthreads();
     }
 
-    // C (slot d) = [+/-] A B  (+ C if acc): three split passes per K step
-    __device__ void issue(int d, int sa, int sb, int neg_a, bool acc) {
-        const uint32_t idesc = make_idesc(fmt, neg_a, npad);
-        const uint32_t dt = slot(d);
-        // the small cross terms for every K step first, then the hi*hi terms:
-        // the cross-term sum is then never added into a large accumulator
-        for (int ks = 0; ks < npad / 16; ++ks) {
-            const uint32_t koff = (uint32_t)ks * 2u * LBO;   // A: 16 columns of K
-            const uint32_t kofb = (uint32_t)ks * 2u * SBO;   // B: 16 rows of K
-            const uint64_t ahi = make_desc(st_addr[sa] + koff);
-            const uint64_t alo = make_desc(st_addr[sa] + HALF_BYTES + koff);
-            const uint64_t bhi = make_desc_b(st_addr[sb] + kofb);
-            const uint64_t blo = make_desc_b(st_addr[sb] + HALF_BYTES + kofb);
-            mma_f16(dt, ahi, blo, idesc, (acc || ks > 0) ? 1u : 0u);
-            mma_f16(dt, alo, bhi, idesc, 1u);
+    __device__ uint64_t da(int sa, uint32_t part, int ks) const {
+        return make_desc(st_addr[sa] + part + (uint32_t)ks * 2u * LBO);   // A: 16 columns of K
+    }
+    __device__ uint64_t db(int sb, uint32_t part, int ks) const {
+        return make_desc_b(st_addr[sb] + part + (uint32_t)ks * 2u * SBO); // B: 16 rows of K
+    }
+
+    // P = A B (acc = false) or P += A B, split in FP16 parts:
+    //   left  += A_lo B_hi  (every K step, first: small terms into a small accumulator)
+    //   left  += A_hi B_hi,  right += A_hi B_lo  (one N = 2 npad instruction per K step)
+    // 2 K + 1 instructions instead of 3 K: an M = 128 instruction costs the
+    // same for any N <= 256.  The product is left + right.
+    __device__ void issue_prod(int sa, int sb, bool acc) {
+        const int K = npad / 16;
+        const uint32_t id1 = make_idesc(fmt, 0, npad), id2 = make_idesc(fmt, 0, 2 * npad);
+        const uint32_t dl = col(pl), dr = col(pr);
+        for (int ks = 0; ks < K; ++ks) mma_f16(dl, da(sa, lo_off, ks), db(sb, 0, ks), id1, (acc || ks > 0) ? 1u : 0u);
+        int k0 = 0;
+        if (!acc) {  // the right half starts fresh
+            mma_f16(dr, da(sa, 0, 0), db(sb, lo_off, 0), id1, 0u);
+            mma_f16(dl, da(sa, 0, 0), db(sb, 0, 0), id1, 1u);
+            k0 = 1;
         }
-        for (int ks = 0; ks < npad / 16; ++ks) {
-            mma_f16(dt, make_desc(st_addr[sa] + (uint32_t)ks * 2u * LBO),
-                    make_desc_b(st_addr[sb] + (uint32_t)ks * 2u * SBO), idesc, 1u);
-        }
+        for (int ks = k0; ks < K; ++ks) mma_f16(dl, da(sa, 0, ks), db(sb, 0, ks), id2, 1u);
+    }
+
+    // left = A_hi B_hi only (a product that only seeds an iteration)
+    __device__ void issue_hh(int sa, int sb) {
+        const int K = npad / 16;
+        const uint32_t id1 = make_idesc(fmt, 0, npad);
+        for (int ks = 0; ks < K; ++ks) mma_f16(col(pl), da(sa, 0, ks), db(sb, 0, ks), id1, ks > 0 ? 1u : 0u);
     }
 
     // wait for every MMA issued so far by thread 0
@@ -388,87 +430,145 @@ struct Kernel {
         return c.abort == 0;
     }
 
-    // one product C = A B into slot d (operands already staged)
-    __device__ bool gemm(int d, int sa, int sb, int neg_a = 0, bool acc = false) {
+    // one product P = A B (P += A B with acc; hi parts only with hh) of
+    // staged operands sa, sb
+    __device__ bool gemm(int sa, int sb, bool acc = false, bool hh = false) {
         sync_for_mma();
         if (threadIdx.x == 0) {
             fence_after();
-            issue(d, sa, sb, neg_a, acc);
+            if (hh) issue_hh(sa, sb);
+            else issue_prod(sa, sb, acc);
         }
         return wait_mma();
     }
 
+    // two products P = A1 B1 + A2 B2
+    __device__ bool gemm2(int sa1, int sb1, int sa2, int sb2) {
+        sync_for_mma();
+        if (threadIdx.x == 0) {
+            fence_after();
+            issue_prod(sa1, sb1, false);
+            issue_prod(sa2, sb2, true);
+        }
+        return wait_mma();
+    }
+
+    // 16 columns of row `row` of staged operand sg as FP32 (hi + lo, exact),
+    // in staged units
+    __device__ void load_staged16(int sg, int c0, float (&v)[16]) const {
+        const uint8_t* p0 = st[sg] + elem_off(row, c0);
+        const uint8_t* p1 = st[sg] + elem_off(row, c0 + 8);
+        const uint4 q[4] = {*(const uint4*)p0, *(const uint4*)p1, *(const uint4*)(p0 + lo_off),
+                            *(const uint4*)(p1 + lo_off)};
+        const uint32_t* w = (const uint32_t*)q;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float2 h, l;
+            if (fmt == 0) {
+                h = __half22float2(*(const __half2*)&w[j]);
+                l = __half22float2(*(const __half2*)&w[8 + j]);
+            } else {
+                h = __bfloat1622float2(*(const __nv_bfloat162*)&w[j]);
+                l = __bfloat1622float2(*(const __nv_bfloat162*)&w[8 + j]);
+            }
+            v[2 * j] = h.x + l.x;
+            v[2 * j + 1] = h.y + l.y;
+        }
+    }
+
+    // issue the TMEM loads of one source for chunk c0 (no wait)
+    __device__ void src_issue(const Src& q, int c0, uint32_t (&r1)[16], uint32_t (&r2)[16]) const {
+        if (q.kind == SRC_TMEM || q.kind == SRC_PAIR) tmem_ld16_issue(col(q.c) + lane_off + c0, r1);
+        if (q.kind == SRC_PAIR) tmem_ld16_issue(col(q.c2) + lane_off + c0, r2);
+    }
+
+    // value of one source for chunk c0 after the wait, times k (target units)
+    __device__ void src_value(const Src& q, float k, int c0, uint32_t (&r1)[16], uint32_t (&r2)[16],
+                              float (&v)[16]) const {
+        if (q.kind == SRC_STAGED) {
+            load_staged16(q.stage, c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] *= k;
+            return;
+        }
+        pin16(r1);
+        if (q.kind == SRC_PAIR) {
+            pin16(r2);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = (__uint_as_float(r1[j]) + __uint_as_float(r2[j])) * k;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r1[j]) * k;
+        }
+    }
+
     // Row-wise combination over this thread's 16-column chunks:
-    //   u = (ca T[sA] + cd I) + cb T[sB]   (cd on the diagonal of the n x n block)
-    // written to FP32 slot `out` (TMEM units), staged operand `sg` and/or the
-    // global FP32 128 x 128 block `gdst` (values, in column groups of four:
-    // element (r, c) at ((c / 4) * 128 + r) * 4 + c % 4); sB = -1 drops the
-    // second term.  Every slot is exactly zero outside the n x n block (the
-    // staged operands are), so only the identity needs masking.  The
-    // power-of-two unit changes are folded into the coefficients.
-    __device__ void combine(int sA, float ca, int sB, float cb, float cd, int out, int sg, float* gdst) {
+    //   u = (A + cd I) + B   (A, B: sources with their coefficients; cd on the
+    //   diagonal of the n x n block)
+    // written to the FP32 TMEM region at column `out` (TMEM units; < 0: none),
+    // staged operand `sg` and/or the global FP32 128 x 128 block `gdst`
+    // (values, in column groups of four: element (r, c) at
+    // ((c / 4) * 128 + r) * 4 + c % 4).  Every TMEM region and staged operand
+    // is exactly zero outside the n x n block, so only the identity needs
+    // masking.  The power-of-two unit changes are folded into the coefficients.
+    __device__ void combine(const Src& A, const Src& B, float cd, int out, int sg, float* gdst) {
         const bool stage_only = out < 0 && gdst == nullptr;
-        const float unit = stage_only ? STAGE_SCALE * TMEM_INV : 1.f;
-        const float ka = ca * unit, kb = cb * unit, kd = cd * TMEM_SCALE * unit;
+        const float unit = stage_only ? STAGE_SCALE * TMEM_INV : 1.f;  // TMEM units -> target units
+        const float ka = A.k * (A.kind == SRC_STAGED ? unit * TMEM_SCALE / STAGE_SCALE : unit);
+        const float kb = B.k * (B.kind == SRC_STAGED ? unit * TMEM_SCALE / STAGE_SCALE : unit);
+        const float kd = cd * TMEM_SCALE * unit;
         const bool diag = cd != 0.f && row < n;
-        const bool two = sB >= 0;
-        const uint32_t ta = slot(sA) + lane_off, tb = slot(two ? sB : sA) + lane_off;
         for (int ch = ch0; ch < ch1; ++ch) {
-            uint32_t u[16], w[16];
-            tmem_ld16_issue(ta + 16 * ch, u);
-            if (two) tmem_ld16_issue(tb + 16 * ch, w);
-            tmem_wait_ld();
-            pin16(u);
-            if (two) pin16(w);
-            combine_chunk(16 * ch, u, w, two, ka, kb, kd, diag, out, sg, gdst, stage_only);
+            const int c0 = 16 * ch;
+            uint32_t a1[16], a2[16], b1[16], b2[16];
+            src_issue(A, c0, a1, a2);
+            src_issue(B, c0, b1, b2);
+            const bool tm = A.kind == SRC_TMEM || A.kind == SRC_PAIR || B.kind == SRC_TMEM || B.kind == SRC_PAIR;
+            if (tm) tmem_wait_ld();
+            float u[16];
+            src_value(A, ka, c0, a1, a2, u);
+            if (diag && (unsigned)(row - c0) < 16u) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (c0 + j == row) u[j] += kd;
+            }
+            if (B.kind != SRC_NONE) {
+                float w[16];
+                src_value(B, kb, c0, b1, b2, w);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) u[j] += w[j];
+            }
+            if (out >= 0) tmem_st16(col((uint32_t)out) + lane_off + c0, u);
+            if (sg >= 0) {
+                if (stage_only) {
+                    stage_chunk(st[sg], row, c0, u, fmt, lo_off);
+                } else {
+                    float t[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) t[j] = u[j] * (STAGE_SCALE * TMEM_INV);
+                    stage_chunk(st[sg], row, c0, t, fmt, lo_off);
+                }
+            }
+            if (gdst) {
+#pragma unroll
+                for (int j = 0; j < 16; j += 4)
+                    *(float4*)(gdst + ((size_t)((c0 + j) >> 2) * NMAX + row) * 4) = make_float4(
+                        u[j] * TMEM_INV, u[j + 1] * TMEM_INV, u[j + 2] * TMEM_INV, u[j + 3] * TMEM_INV);
+            }
         }
         if (out >= 0) tmem_wait_st();
     }
 
-    __device__ __forceinline__ void combine_chunk(int c0, const uint32_t (&ur)[16], const uint32_t (&wr)[16], bool two,
-                                                  float ka, float kb, float kd, bool diag, int out, int sg,
-                                                  float* gdst, bool stage_only) {
-        float u[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) u[j] = __uint_as_float(ur[j]) * ka;
-        if (diag && (unsigned)(row - c0) < 16u) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-                if (c0 + j == row) u[j] += kd;
-        }
-        if (two) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) u[j] = fmaf(kb, __uint_as_float(wr[j]), u[j]);
-        }
-        if (out >= 0) tmem_st16(slot(out) + lane_off + c0, u);
-        if (sg >= 0) {
-            if (stage_only) {
-                stage_chunk(st[sg], row, c0, u, fmt);
-            } else {
-                float t[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) t[j] = u[j] * (STAGE_SCALE * TMEM_INV);
-                stage_chunk(st[sg], row, c0, t, fmt);
-            }
-        }
-        if (gdst) {
-#pragma unroll
-            for (int j = 0; j < 16; j += 4)
-                *(float4*)(gdst + ((size_t)((c0 + j) >> 2) * NMAX + row) * 4) =
-                    make_float4(u[j] * TMEM_INV, u[j + 1] * TMEM_INV, u[j + 2] * TMEM_INV, u[j + 3] * TMEM_INV);
-        }
-    }
-
-    // largest k <= kmax with 4^k max_r sum_c |T[sl]_rc| <= 1 (block-uniform).
-    // Row sums and their maximum in FP32; the factor 1 + 2^-16 covers the
-    // sums' rounding, so the bound stays an upper bound.
-    __device__ int fewer_steps(int sl, int kmax) {
+    // largest k <= kmax with 4^k max_r sum_c |P_rc| <= 1 for the product P
+    // (block-uniform).  Row sums and their maximum in FP32; the factor
+    // 1 + 2^-16 covers the sums' rounding, so the bound stays an upper bound.
+    __device__ int fewer_steps(int kmax) {
         float rs = 0.f;
         for (int ch = ch0; ch < ch1; ++ch) {
-            float v[16];
-            tmem_ld16(slot(sl) + lane_off + ch * 16, v);
+            float v[16], w[16];
+            tmem_ld16x2(col(pl) + lane_off + ch * 16, col(pr) + lane_off + ch * 16, v, w);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) rs += fabsf(v[j]);
+            for (int j = 0; j < 16; ++j) rs += fabsf(v[j] + w[j]);
         }
         c.red[threadIdx.x] = rs;
         __syncthreads();
@@ -500,7 +600,7 @@ struct Kernel {
     // row-indexed stores are conflict-free); the caller adds them after a
     // barrier.
     template <int NC>
-    __device__ void rowvec(int sl, float scale, const float* v, FF* P) {
+    __device__ void rowvec(uint32_t sl, float scale, const float* v, FF* P) {
         constexpr int VL = NC + 4;
         float hi[NC], lo[NC];  // chunk sums accumulated as unevaluated float pairs
 #pragma unroll
@@ -508,7 +608,7 @@ struct Kernel {
         for (int ch = ch0; ch < ch1; ++ch) {
             const int c0 = ch * 16;
             float m[16];
-            tmem_ld16(slot(sl) + lane_off + c0, m);
+            tmem_ld16(col(sl) + lane_off + c0, m);
             float acc[NC];
 #pragma unroll
             for (int cc = 0; cc < NC; ++cc) acc[cc] = 0.f;
@@ -554,7 +654,7 @@ struct Kernel {
     // Writes d = (I - Z_s)/2 on the core columns and its core diagonal terms.
     // Scratch: staged operands S0 and S1 (free at this point).  All threads.
     template <int NC>
-    __device__ void refine_core(int zs, int xs, float zsc, int ncore) {
+    __device__ void refine_core(uint32_t zs, uint32_t xs, float zsc, int ncore) {
         constexpr int VL = NC + 4;
         float* Vz = (float*)st[0];
         float* Vw = Vz + NMAX * VL;
@@ -574,7 +674,7 @@ struct Kernel {
             float x[NC];
             if (grp == 0) {
                 float zv[NC];
-                tmem_ld_cols<NC>(slot(zs) + lane_off, c.cpos + b0, nc, zv);
+                tmem_ld_cols<NC>(col(zs) + lane_off, c.cpos + b0, nc, zv);
 #pragma unroll
                 for (int cc = 0; cc < NC; ++cc) x[cc] = (row < n && cc < nc) ? zv[cc] * zsc : 0.f;
                 put_row<NC>(Vz, x);
@@ -648,40 +748,43 @@ struct Kernel {
         }
     }
 
-    // core columns of slot sl (TMEM words) times k into out[ocol + row]; on
-    // the core diagonal the word times tk goes to trace term `term`.  Warps of
-    // column group 0.
-    __device__ void core_columns(int sl, int ncore, float k, double* out, int term, float tk) {
+    // core columns of the product P (left + right, TMEM words) times k into
+    // out[ocol + row]; on the core diagonal the word times tk goes to trace
+    // term `term`.  Warps of column group 0.
+    __device__ void core_columns(int ncore, float k, double* out, int term, float tk) {
         if (grp != 0) return;
         for (int b0 = 0; b0 < ncore; b0 += 16) {
             const int nc = min(16, ncore - b0);
-            float g[16];
-            tmem_ld_cols<16>(slot(sl) + lane_off, c.cpos + b0, nc, g);
+            float g[16], h[16];
+            tmem_ld_cols<16>(col(pl) + lane_off, c.cpos + b0, nc, g);
+            tmem_ld_cols<16>(col(pr) + lane_off, c.cpos + b0, nc, h);
             if (row < n) {
 #pragma unroll
                 for (int cc = 0; cc < 16; ++cc) {
                     if (cc < nc) {
-                        out[c.ocol[b0 + cc] + row] = f2d(g[cc] * k);
-                        if (row == c.cpos[b0 + cc]) c.tv[term][b0 + cc] = g[cc] * tk;
+                        const float v = g[cc] + h[cc];
+                        out[c.ocol[b0 + cc] + row] = f2d(v * k);
+                        if (row == c.cpos[b0 + cc]) c.tv[term][b0 + cc] = v * tk;
                     }
                 }
             }
         }
     }
 
-    // largest diagonal word of slot sl over rows < n into c.wred[0..3]
+    // largest diagonal word of the product P over rows < n into c.wred[0..3]
     // (warps of column group 0; a barrier must follow before reading it)
-    __device__ void diag_max(int sl) {
+    __device__ void diag_max() {
         if (grp != 0) return;
         const uint32_t cb = (uint32_t)(row & ~31);
-        float u[16], w[16];
-        tmem_ld16x2(slot(sl) + lane_off + cb, slot(sl) + lane_off + cb + 16, u, w);
+        float u[16], w[16], u2[16], w2[16];
+        tmem_ld16x2(col(pl) + lane_off + cb, col(pl) + lane_off + cb + 16, u, w);
+        tmem_ld16x2(col(pr) + lane_off + cb, col(pr) + lane_off + cb + 16, u2, w2);
         float d = 0.f;
         const int j = row & 31;
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-            d = (j == q) ? u[q] : d;
-            d = (j == q + 16) ? w[q] : d;
+            d = (j == q) ? u[q] + u2[q] : d;
+            d = (j == q + 16) ? w[q] + w2[q] : d;
         }
         d = row < n ? d : 0.f;
         for (int o = 16; o > 0; o >>= 1) d = fmaxf(d, __shfl_down_sync(0xffffffffu, d, o));
@@ -714,7 +817,7 @@ struct Kernel {
                 v[4 * q + 2] = x.z * STAGE_SCALE;
                 v[4 * q + 3] = x.w * STAGE_SCALE;
             }
-            stage_chunk(st[sg], row, c0_of(ch), v, fmt);
+            stage_chunk(st[sg], row, c0_of(ch), v, fmt, lo_off);
         }
     }
 
@@ -746,7 +849,7 @@ struct Kernel {
                 for (int j = 0; j < 16; ++j)
                     if (c0 + j == row) v[j] = dv;
             }
-            stage_chunk(st[sg], row, c0, v, fmt);
+            stage_chunk(st[sg], row, c0, v, fmt, lo_off);
         }
     }
 };
@@ -808,117 +911,99 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
         __syncthreads();
         float* z1base = a.z1pool + (size_t)i * (a.m > 0 ? a.m : 1) * NMAX * NMAX;
 
-        // ---- Taylor start: Q = x0^2, P = I - Q/3 + 2 Q^2/15 (slots: 0 Q, 1 P) ----
+        // ---- Taylor start: Q = x0^2, T = I - Q/3 + 2 Q^2/15 (X region: Q, Z region: T) ----
         const float* hb = a.hblk + a.boff[i];
         K.stage_dense(hb, ldexpf(1.f, -(s + 1)), true, 1.f, 0);          // S0 = x0
-        if (!K.gemm(0, 0, 0)) break;                                      // T0 = Q
+        if (!K.gemm(0, 0)) break;                                         // P = Q
         // rho(x0)^2 = rho(Q) <= max_r sum_c |Q_rc| (Gershgorin on the square is
         // tighter than on h): drop k steps while 2^k x0 keeps spectral radius <= 1
-        const int k = K.fewer_steps(0, s - a.min_steps);
+        const int k = K.fewer_steps(s - a.min_steps);
         float qscale = 1.f;
         if (k > 0) {
             s -= k;
             qscale = ldexpf(1.f, 2 * k);
             K.stage_dense(hb, ldexpf(1.f, -(s + 1)), true, ldexpf(1.f, k), 0);  // S0 = 2^k x0
         }
-        K.combine(0, qscale, -1, 0.f, 0.f, -1, 1, nullptr);               // S1 = Q
-        if (!K.gemm(1, 1, 1)) break;                                      // T1 = Q^2
-        K.combine(0, -qscale / 3.f, 1, 2.f / 15.f, 1.f, 1, -1, nullptr);  // T1 = P
+        K.combine(K.Pk(qscale), K.none(), 0.f, K.xc, 1, nullptr);          // X region = Q, S1 = Q
+        if (!K.gemm(1, 1)) break;                                         // P = Q^2
+        K.combine(K.T(K.xc, -1.f / 3.f), K.Pk(2.f / 15.f), 1.f, K.zc, -1, nullptr);  // Z region = T
         bool ok = true;
         for (int r = 0; r < a.m && ok; ++r) {
             // the perturbation, normalised by sigma_r
             const float* h1b = a.hblk + (int64_t)(1 + r) * a.hblk_stride + a.boff[i];
             const float x1scale = ldexpf(1.f, -(s + 1) - c.sigk[r]);
-            // dZ0 = X1 P + x0 P1,  P1 = -Q1/3 + (2/15)(Q Q1 + Q1 Q),  Q1 = x0 X1 + X1 x0
-            K.stage_dense(h1b, x1scale, false, 0.f, 1);                     // S1 = X1
-            K.sync_for_mma();
-            if (threadIdx.x == 0) {
-                fence_after();
-                K.issue(2, 0, 1, 0, false);
-                K.issue(2, 1, 0, 0, true);
-            }
-            if (!(ok = K.wait_mma())) break;                               // T2 = Q1
-            K.combine(2, 1.f, -1, 0.f, 0.f, -1, 1, nullptr);               // S1 = Q1
-            K.combine(0, qscale, -1, 0.f, 0.f, -1, 2, nullptr);            // S2 = Q
-            K.sync_for_mma();
-            if (threadIdx.x == 0) {
-                fence_after();
-                K.issue(3, 2, 1, 0, false);
-                K.issue(3, 1, 2, 0, true);
-            }
-            if (!(ok = K.wait_mma())) break;                               // T3 = Q Q1 + Q1 Q
-            K.combine(2, -1.f / 3.f, 3, 2.f / 15.f, 0.f, -1, 1, nullptr);  // S1 = P1
-            if (!(ok = K.gemm(2, 0, 1))) break;                            // T2 = x0 P1
-            K.combine(1, 1.f, -1, 0.f, 0.f, -1, 2, nullptr);               // S2 = P
-            K.stage_dense(h1b, x1scale, false, 0.f, 1);                     // S1 = X1
-            if (!(ok = K.gemm(2, 1, 2, 0, true))) break;                   // T2 += X1 P
-            K.combine(2, 1.f, -1, 0.f, 0.f, -1, -1, z1base + (size_t)r * NMAX * NMAX);
+            // dZ0 = X1 T + x0 T1,  T1 = -Q1/3 + (2/15)(Q Q1 + Q1 Q),  Q1 = x0 X1 + X1 x0
+            K.stage_dense(h1b, x1scale, false, 0.f, 1);                   // S1 = X1
+            if (!(ok = K.gemm2(0, 1, 1, 0))) break;                        // P = Q1
+            K.combine(K.Pk(1.f), K.none(), 0.f, -1, 1, nullptr);           // S1 = Q1
+            K.combine(K.T(K.xc, 1.f), K.none(), 0.f, -1, 2, nullptr);      // S2 = Q
+            if (!(ok = K.gemm2(2, 1, 1, 2))) break;                        // P = Q Q1 + Q1 Q
+            K.combine(K.S(1, -1.f / 3.f), K.Pk(2.f / 15.f), 0.f, -1, 1, nullptr);  // S1 = T1
+            if (!(ok = K.gemm(0, 1))) break;                               // P = x0 T1
+            K.combine(K.T(K.zc, 1.f), K.none(), 0.f, -1, 2, nullptr);      // S2 = T
+            K.stage_dense(h1b, x1scale, false, 0.f, 1);                   // S1 = X1
+            if (!(ok = K.gemm(1, 2, true))) break;                         // P += X1 T
+            K.combine(K.Pk(1.f), K.none(), 0.f, -1, -1, z1base + (size_t)r * NMAX * NMAX);
         }
         if (!ok) break;
-        K.combine(1, 1.f, -1, 0.f, 0.f, -1, 2, nullptr);                  // S2 = P
-        if (!K.gemm(2, 0, 2)) break;                                      // T2 = Z0 = x0 P
+        K.combine(K.T(K.zc, 1.f), K.none(), 0.f, -1, 2, nullptr);          // S2 = T
+        if (!K.gemm(0, 2)) break;                                         // P = Z0 = x0 T
+        K.combine(K.Pk(1.f), K.none(), 0.f, K.zc, -1, nullptr);            // Z region = Z0
 
-        // ---- doublings ----
-        int zs = 2;
-        float zscale = 1.f;
+        // ---- doublings: Z <- 2 X Z, X = (I + Z^2)^-1 ----
         for (int step = 0; step < s && ok; ++step) {
-            int fr[3], q = 0;
-            for (int k = 0; k < 4; ++k)
-                if (k != zs) fr[q++] = k;
-            const int ys = fr[0], ts = fr[1], xs = fr[2];
-            K.combine(zs, zscale, -1, 0.f, 0.f, -1, 0, nullptr);                        // S0 = Z
-            if (!(ok = K.gemm(ys, 0, 0))) break;                                        // Y
-            K.combine(ys, 1.f, -1, 0.f, 0.f, -1, 1, nullptr);                           // S1 = Y
-            if (!(ok = K.gemm(ts, 1, 1))) break;                                        // Y^2
-            K.combine(ys, -80.f / 99.f, ts, 32.f / 99.f, 98.f / 99.f, xs, 2, nullptr);  // X0
+            const bool last = step == s - 1;
+            K.combine(K.T(K.zc, 1.f), K.none(), 0.f, -1, 0, nullptr);              // S0 = Z
+            if (!(ok = K.gemm(0, 0))) break;                                       // P = Y = Z^2
+            K.combine(K.Pk(1.f), K.none(), 0.f, -1, 1, nullptr);                   // S1 = Y
+            if (!(ok = K.gemm(1, 1, false, true))) break;                          // P = Y^2 (hi parts)
+            K.combine(K.S(1, -80.f / 99.f), K.T(K.pl, 32.f / 99.f), 98.f / 99.f, K.xc, 2, nullptr);  // X0
             for (int j = 0; j < a.ns_iters && ok; ++j) {
-                if (!(ok = K.gemm(ts, 1, 2))) break;                                    // T = Y X
-                K.combine(xs, -1.f, ts, -1.f, 1.f, -1, 0, nullptr);                     // S0 = R = (I - X) - Y X
-                if (!(ok = K.gemm(xs, 2, 0, 0, true))) break;                           // X += X R
-                K.combine(xs, 1.f, -1, 0.f, 0.f, -1, 2, nullptr);                       // S2 = X
+                if (!(ok = K.gemm(1, 2))) break;                                   // P = Y X
+                K.combine(K.T(K.xc, -1.f), K.Pk(-1.f), 1.f, -1, 0, nullptr);       // S0 = R = (I - X) - Y X
+                if (!(ok = K.gemm(2, 0))) break;                                   // P = X R
+                K.combine(K.T(K.xc, 1.f), K.Pk(1.f), 0.f, K.xc, 2, nullptr);       // X += X R, S2 = X
             }
             if (!ok) break;
-            K.combine(zs, zscale, -1, 0.f, 0.f, -1, 0, nullptr);                        // S0 = Z
-            if (!(ok = K.gemm(ts, 2, 0))) break;                                        // W / 2 = X Z
-            if (step == s - 1) {
-                // ---- the last doubling redone on the core columns (CUDA cores) ----
-                const float zsc = zscale * TMEM_INV;
-                if (ncore <= 8) K.refine_core<8>(zs, xs, zsc, ncore);
-                else K.refine_core<16>(zs, xs, zsc, ncore);
+            if (last) {
                 // d (I - d) = (I - Z_s^2) / 4 = ((I - Y) X)^2 / 4: no cancellation
                 // near saturation (Y = Z_{s-1}^2, X = (I + Y)^-1)
-                K.combine(ys, -1.f, -1, 0.f, 1.f, -1, 1, nullptr);                      // S1 = I - Y
-                if (!(ok = K.gemm(zs, 1, 2))) break;                                    // G = (I - Y) X
-                K.combine(zs, 1.f, -1, 0.f, 0.f, -1, 1, nullptr);                       // S1 = G
-                if (!(ok = K.gemm(ys, 1, 1))) break;                                    // G^2
-                K.core_columns(ys, ncore, (float)(0.25 * a.beta) * TMEM_INV, a.d1mu_val, T_DD,
-                               0.25f * TMEM_INV);                                        // d1_mu = beta G^2 / 4
-                K.diag_max(ys);
+                K.combine(K.S(1, -1.f), K.none(), 1.f, -1, 1, nullptr);            // S1 = I - Y
+                if (!(ok = K.gemm(1, 2))) break;                                   // P = G = (I - Y) X
+                K.combine(K.Pk(1.f), K.none(), 0.f, -1, 1, nullptr);               // S1 = G
+                if (!(ok = K.gemm(1, 1))) break;                                   // P = G^2
+                K.core_columns(ncore, (float)(0.25 * a.beta) * TMEM_INV, a.d1mu_val, T_DD,
+                               0.25f * TMEM_INV);                                  // d1_mu = beta G^2 / 4
+                K.diag_max();
             }
-            if (a.m > 0) K.combine(ts, 2.f, -1, 0.f, 0.f, -1, 0, nullptr);              // S0 = W
+            K.combine(K.T(K.zc, 1.f), K.none(), 0.f, -1, 0, nullptr);              // S0 = Z
+            if (!(ok = K.gemm(2, 0))) break;                                       // P = W / 2 = X Z
+            if (last) {
+                // ---- the last doubling redone on the core columns (CUDA cores) ----
+                if (ncore <= 8) K.refine_core<8>(K.zc, K.xc, TMEM_INV, ncore);
+                else K.refine_core<16>(K.zc, K.xc, TMEM_INV, ncore);
+                if (a.m > 0) K.combine(K.Pk(2.f), K.none(), 0.f, -1, 0, nullptr);  // S0 = W
+            } else {
+                K.combine(K.Pk(2.f), K.none(), 0.f, K.zc, a.m > 0 ? 0 : -1, nullptr);  // Z region = W (next Z), S0 = W
+            }
             for (int r = 0; r < a.m && ok; ++r) {
+                // Z1 <- 2 X Z1 X - (W Z1 / 2) W
                 float* z1 = z1base + (size_t)r * NMAX * NMAX;
-                K.stage_global(z1, 1);                                                  // S1 = Z1
-                K.sync_for_mma();
-                if (threadIdx.x == 0) {
-                    fence_after();
-                    K.issue(ys, 2, 1, 0, false);                                        // X Z1
-                    K.issue(zs, 0, 1, 0, false);                                        // W Z1
-                }
-                if (!(ok = K.wait_mma())) break;
-                K.combine(ys, 2.f, -1, 0.f, 0.f, -1, 1, nullptr);                       // S1 = 2 X Z1
-                if (!(ok = K.gemm(ys, 1, 2))) break;                                    // 2 X Z1 X
-                K.combine(zs, -0.5f, -1, 0.f, 0.f, -1, 1, nullptr);                     // S1 = -W Z1 / 2
-                if (!(ok = K.gemm(ys, 1, 0, 0, true))) break;                           // - W Z1 W / 2
-                if (step < s - 1) {
-                    K.combine(ys, 1.f, -1, 0.f, 0.f, -1, -1, z1);                       // Z1 -> global
+                K.stage_global(z1, 1);                                             // S1 = Z1
+                if (!(ok = K.gemm(2, 1))) break;                                   // P = X Z1
+                K.combine(K.Pk(2.f), K.none(), 0.f, K.xc, -1, nullptr);            // X region = 2 X Z1
+                if (!(ok = K.gemm(0, 1))) break;                                   // P = W Z1
+                K.combine(K.Pk(-0.5f), K.none(), 0.f, -1, 1, nullptr);             // S1 = -W Z1 / 2
+                if (!(ok = K.gemm(1, 0))) break;                                   // P = -(W Z1 / 2) W
+                K.combine(K.T(K.xc, 1.f), K.none(), 0.f, -1, 1, nullptr);          // S1 = 2 X Z1
+                if (!(ok = K.gemm(1, 2, true))) break;                             // P += (2 X Z1) X
+                if (!last) {
+                    K.combine(K.Pk(1.f), K.none(), 0.f, -1, -1, z1);               // Z1 -> global
                 } else {
-                    const float sc = -ldexpf(0.5f, c.sigk[r]) * TMEM_INV;               // d1_lambda = -Z1_s / (2 sigma)
-                    K.core_columns(ys, ncore, sc, a.D1val[r], T_L0 + r, sc);
+                    const float sc = -ldexpf(0.5f, c.sigk[r]) * TMEM_INV;          // d1_lambda = -Z1_s / (2 sigma)
+                    K.core_columns(ncore, sc, a.D1val[r], T_L0 + r, sc);
                 }
             }
-            zs = ts;
-            zscale = 2.f;
         }
         if (!ok) break;
 
