@@ -539,9 +539,14 @@ def main():
 
 
 def workload_text(wl, system):
+    graph = (f"two-pass graph |H| > {wl.tau:g} or |D_1| > {wl.tau:g} (D_1 from a first solve on the H graph)")
+    if system.meta.get("kind") == "chains":
+        return (f"{system.n_atoms} atoms ({system.meta['n_chains']} C/N/O chains of {system.meta['chain_len']} "
+                f"heavy atoms with H caps, {system.meta['n_waters']} H2O; {system.n_orb} orbitals), periodic box "
+                f"{system.box:.1f} A, sp tight binding, kT {wl.kT} eV, {graph}, cores of ~{wl.core_atoms} atoms by "
+                f"coordinate bisection (cores over {SUB_CAP} orbitals split into atoms, then orbitals), one H1")
     return (f"{system.meta.get('n_waters')} H2O ({system.n_orb} orbitals), periodic box "
-            f"{system.box:.1f} A, sp tight binding, kT {wl.kT} eV, two-pass graph |H| > {wl.tau:g} or "
-            f"|D_1| > {wl.tau:g} (D_1 from a first solve on the H graph), one molecule per core (cores "
+            f"{system.box:.1f} A, sp tight binding, kT {wl.kT} eV, {graph}, one molecule per core (cores "
             f"over {SUB_CAP} orbitals split into atoms), one H1")
 
 

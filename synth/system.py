@@ -74,6 +74,7 @@ class System:
     orb_atom: np.ndarray            # (n_orb,) int32 atom of each orbital
     H: CSR                          # orthogonal TB Hamiltonian, eV
     n_electrons: int                # neutral valence electron count
+    atom_core: np.ndarray | None = None  # (n_atoms,) core id of each atom, when not one per molecule
     meta: dict = field(default_factory=dict)
 
     @property
@@ -91,8 +92,9 @@ class System:
 
     @property
     def orb_group(self) -> np.ndarray:
-        """Molecule id of every orbital (one core per molecule)."""
-        return self.molecule[self.orb_atom].astype(np.int32)
+        """Core id of every orbital: its atom's core when set, else its molecule."""
+        owner = self.atom_core if self.atom_core is not None else self.molecule
+        return owner[self.orb_atom].astype(np.int32)
 
     @property
     def z_valence(self) -> np.ndarray:

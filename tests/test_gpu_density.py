@@ -205,6 +205,33 @@ def test_two_pass_graph_capped_partition(gb, precision):
     assert eD <= TOL[precision] and eD1 <= TOL[precision]
 
 
+def test_heterogeneous_chains(gb):
+    # a C/N/O chain with H caps in water: coordinate-bisection cores of ~30
+    # atoms give subgraphs of 227-367 orbitals on the FP64 path; the capped
+    # partition (atoms, then orbitals) brings them under 128 for the split path
+    wl, system, h1 = make_workload("chains_small", n_rhs=1)
+    H = system.H
+    Hd, H1d = to_device(H), [to_device(h1[0])]
+    adj = o_graph(H.n, H.indptr, H.indices, H.data, wl.tau)
+    G = gb.graph_build(Hd, wl.tau)
+    groups, atoms = torch.as_tensor(system.orb_group), torch.as_tensor(system.orb_atom)
+    part = o_part(adj, system.orb_group)
+    assert part.sizes().max() > 128
+    ref = oracle_graph(H, h1, wl.kT, system.n_occ, part, workers=4)
+    R = gb.density_and_response(Hd, H1d, wl.kT, system.n_electrons, gb.partition(G, groups), precision="fp64")
+    eD, eD1 = max_abs_block_error(R, ref, part)
+    assert eD <= TOL["fp64"] and eD1 <= TOL["fp64"]
+    capped = o_part_capped(adj, system.orb_group, system.orb_atom, 128)
+    refc = oracle_graph(H, h1, wl.kT, system.n_occ, capped, workers=4)
+    P = gb.partition(G, groups, subgroups=atoms, max_sub=128)
+    assert P.max_sub <= 128 and P.n_sub == capped.n_sub
+    for prec in ("fp64", "fp16x3"):
+        R = gb.density_and_response(Hd, H1d, wl.kT, system.n_electrons, P, precision=prec)
+        eD, eD1 = max_abs_block_error(R, refc, capped)
+        print(f"chains {prec}: n_sub {P.n_sub} max|dD|={eD:.2e} max|dD1|={eD1:.2e}")
+        assert eD <= TOL[prec] and eD1 <= TOL[prec]
+
+
 def test_single_subgraph_equals_full(gb):
     # one core holding everything: the graph method is the full calculation
     Hc, H1c = _random_system(100, 11, density=0.1)
