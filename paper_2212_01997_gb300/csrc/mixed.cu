@@ -6,9 +6,10 @@
 //   A_hi B_hi + A_hi B_lo + A_lo B_hi
 // with FP32 accumulation in tensor memory.  An M = 128 tcgen05.mma costs the
 // same for any N <= 256, so A_hi B_hi and A_hi B_lo share one instruction of
-// N = 2 npad ([B_hi | B_lo] staged side by side): 2 K + 1 instructions per
+// N = 2 npad ([B_hi | B_lo] staged side by side): 2 K instructions per
 // product instead of 3 K.  The product P lands in two TMEM halves (left:
-// A_hi B_hi + A_lo B_hi, right: A_hi B_lo) that the staging pass adds.
+// A_hi B_hi, right: the cross terms A_hi B_lo + A_lo B_hi) that the staging
+// pass adds.
 // Quantities close to the identity never pass through the 16-bit parts: the
 // Newton-Schulz residual R = (I - X) - Y X is formed in FP32 from the FP32 X
 // and the product (I - X exact on the diagonal, where X is in [1/2, 1]).
@@ -390,23 +391,20 @@ struct Kernel {
         return make_desc_b(st_addr[sb] + part + (uint32_t)ks * 2u * SBO); // B: 16 rows of K
     }
 
-    // P = A B (acc = false) or P += A B, split in FP16 parts:
-    //   left  += A_lo B_hi  (every K step, first: small terms into a small accumulator)
-    //   left  += A_hi B_hi,  right += A_hi B_lo  (one N = 2 npad instruction per K step)
-    // 2 K + 1 instructions instead of 3 K: an M = 128 instruction costs the
-    // same for any N <= 256.  The product is left + right.
+    // P = A B (acc = false) or P += A B, split in FP16 parts, per K step:
+    //   [left | right] += A_hi [B_hi | B_lo]   (one N = 2 npad instruction)
+    //   right          += A_lo B_hi
+    // 2 K instructions instead of 3 K: an M = 128 instruction costs the same
+    // for any N <= 256.  The left accumulator holds only the large A_hi B_hi
+    // terms, the right one the small cross terms; the product is left + right.
     __device__ void issue_prod(int sa, int sb, bool acc) {
         const int K = npad / 16;
         const uint32_t id1 = make_idesc(fmt, 0, npad), id2 = make_idesc(fmt, 0, 2 * npad);
         const uint32_t dl = col(pl), dr = col(pr);
-        for (int ks = 0; ks < K; ++ks) mma_f16(dl, da(sa, lo_off, ks), db(sb, 0, ks), id1, (acc || ks > 0) ? 1u : 0u);
-        int k0 = 0;
-        if (!acc) {  // the right half starts fresh
-            mma_f16(dr, da(sa, 0, 0), db(sb, lo_off, 0), id1, 0u);
-            mma_f16(dl, da(sa, 0, 0), db(sb, 0, 0), id1, 1u);
-            k0 = 1;
+        for (int ks = 0; ks < K; ++ks) {
+            mma_f16(dl, da(sa, 0, ks), db(sb, 0, ks), id2, (acc || ks > 0) ? 1u : 0u);
+            mma_f16(dr, da(sa, lo_off, ks), db(sb, 0, ks), id1, 1u);
         }
-        for (int ks = k0; ks < K; ++ks) mma_f16(dl, da(sa, 0, ks), db(sb, 0, ks), id2, 1u);
     }
 
     // left = A_hi B_hi only (a product that only seeds an iteration)
