@@ -498,8 +498,8 @@ def main():
             "peak_source": ("measured bf16 dense burst (MEASURED_PEAKS.json); the fp16 dense rate is the "
                             "same nominal figure" if "bf16_tflops" in peaks else "fallback 1.9 PFLOP/s bf16"),
             "kernel_ms_per_launch": head["kernel_ms"], "algorithmic_flops_per_launch": head["flops"],
-            "flop_count": "2 |S_i|^3 per matrix product of the recursion, summed over subgraphs; the three "
-                          "split passes and the padding to 128 rows are not counted"}
+            "flop_count": "2 |S_i|^3 per matrix product of the recursion, summed over subgraphs; the split "
+                          "terms and the padding to 128 rows are not counted"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload)

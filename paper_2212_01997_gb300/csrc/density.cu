@@ -364,7 +364,7 @@ struct DensityLayout {
     int64_t* scan_tmp;
     int* err;
     double* pool;       // FP64: (NBUF + m) * pool_stride
-    float* z1pool;      // split: n_sub * m * 128 * 128
+    float* z1pool;      // split: min(n_sub, GB_SPLIT_MAX_CTAS) * m * 128 * 128 (per CTA)
     float* hblk;        // split: (1 + m) * pool_stride dense gathered blocks (FP32)
     double* hdiag;      // split: sub_nnz FP64 diagonals of h^(i)
     double* h1max;      // split: n_sub * m largest |h1| row sums
@@ -398,7 +398,8 @@ DensityLayout layout_density(Arena& ar, const gb_part* P, int32_t m, int precisi
         // vector loads of the staging code)
         L.pool_stride = (((int64_t)P->max_sub + 15) * (P->sub_nnz + 15 * n_sub) + 32 + 63) & ~(int64_t)63;
         L.pool = nullptr;
-        L.z1pool = ar.take<float>(n_sub * (int64_t)(m > 0 ? m : 1) * GB_SPLIT_MAX_N * GB_SPLIT_MAX_N);
+        const int64_t ctas = n_sub < GB_SPLIT_MAX_CTAS ? n_sub : GB_SPLIT_MAX_CTAS;
+        L.z1pool = ar.take<float>(ctas * (int64_t)(m > 0 ? m : 1) * GB_SPLIT_MAX_N * GB_SPLIT_MAX_N);
         L.hblk = ar.take<float>((1 + m) * L.pool_stride);
         L.hdiag = ar.take<double>(P->sub_nnz);
         L.h1max = ar.take<double>(n_sub * (int64_t)(m > 0 ? m : 1));

@@ -8,6 +8,9 @@
 
 constexpr int GB_MAX_RHS = 8;
 constexpr int GB_SPLIT_MAX_N = 128;  // largest subgraph of the tensor-core kernel
+// most CTAs of the persistent tensor-core kernel (one per SM); each owns one
+// FP32 response scratch of m x 128 x 128
+constexpr int GB_SPLIT_MAX_CTAS = 256;
 
 // Per-subgraph trace slots (tr[i * tr_stride + k])
 // TR_MAXW is reduced with max (the largest diagonal element of d1_mu over all

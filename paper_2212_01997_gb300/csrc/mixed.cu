@@ -66,6 +66,7 @@ enum CoreTerm { T_DHI = 0, T_DLO = 1, T_DD = 2, T_L0 = 3, T_COUNT = 3 + GB_MAX_R
 
 struct __align__(16) Ctl {
     unsigned long long mbar;
+    unsigned long long mbar_bulk;  // completion of the bulk copy into a staged operand
     uint32_t tmem_base;
     int abort;
     int s;                      // the current subgraph's step count
@@ -133,6 +134,22 @@ __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// orders this thread's generic global writes before later async-proxy
+// (bulk copy) reads of them
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// one bulk copy global -> shared of `bytes` (multiple of 16, both addresses
+// 16-byte aligned), completing on the mbarrier's transaction count
+__device__ __forceinline__ void bulk_g2s(uint32_t sdst, const void* gsrc, uint32_t bytes, uint32_t mbar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sdst),
+        "l"(gsrc), "r"(bytes), "r"(mbar)
+        : "memory");
+}
+
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
     for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
         uint32_t done;
@@ -166,23 +183,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// 16-column load without the wait (registers defined only after
-// tmem_wait_ld + pin16)
-__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-        "%12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
+// waits for every tcgen05.ld this thread issued
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-// keeps every use of r behind the preceding wait
-__device__ __forceinline__ void pin16(uint32_t (&r)[16]) {
-#pragma unroll
-    for (int j = 0; j < 16; ++j) asm volatile("" : "+r"(r[j]));
-}
 
 // two 16-column loads (e.g. the same chunk of two slots) behind one wait
 __device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float (&u)[16], float (&w)[16]) {
@@ -228,19 +230,6 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t base, const int32_t* cols,
         asm volatile("" : "+r"(r[q]));
         v[q] = __uint_as_float(r[q]);
     }
-}
-
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-        "%12, %13, %14, %15, %16};" ::"r"(taddr),
-        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
-        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
-        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
-        "r"(__float_as_uint(v[15]))
-        : "memory");
 }
 
 // completes every tcgen05.st this thread issued
@@ -311,13 +300,51 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
 }
 __device__ __forceinline__ FF ff_neg(FF a) { return {-a.hi, -a.lo}; }
 
-enum SrcKind { SRC_NONE = 0, SRC_TMEM = 1, SRC_PAIR = 2, SRC_STAGED = 3 };
-struct Src {
-    int kind;
-    uint32_t c, c2;  // TMEM columns (SRC_TMEM; SRC_PAIR: left, right)
-    int stage;       // SRC_STAGED
-    float k;         // coefficient
+// combine sources, each times a coefficient k: nothing, one FP32 TMEM region
+// (column c), the packed product (left c + right c2), a staged operand (hi +
+// lo).  Distinct types, so every combine is compiled for its own sources.
+struct SrcN {
+    static constexpr int loads = 0;
+    static constexpr bool staged = false;
+    float k;
 };
+struct SrcT {
+    static constexpr int loads = 1;
+    static constexpr bool staged = false;
+    uint32_t c;
+    float k;
+};
+struct SrcP {
+    static constexpr int loads = 2;
+    static constexpr bool staged = false;
+    uint32_t c, c2;
+    float k;
+};
+struct SrcS {
+    static constexpr int loads = 0;
+    static constexpr bool staged = true;
+    int stage;
+    float k;
+};
+
+// 8-column TMEM loads (32 lanes x 8 columns per warp), issued without a wait
+__device__ __forceinline__ void tmem_ld8_issue(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void pin8(uint32_t (&r)[8]) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) asm volatile("" : "+r"(r[j]));
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
 
 struct Kernel {
     const PassArgs& a;
@@ -327,6 +354,8 @@ struct Kernel {
     uint32_t tbase;
     uint32_t mbar;
     uint32_t phase;
+    uint32_t mbar_bulk;
+    uint32_t phase_bulk;
     int fmt;
     int n, npad;
     int row;       // this thread's row = TMEM lane
@@ -343,6 +372,8 @@ struct Kernel {
         }
         mbar = smem_u32(&c.mbar);
         phase = 0;
+        mbar_bulk = smem_u32(&c.mbar_bulk);
+        phase_bulk = 0;
         fmt = a.split_kind;
         row = threadIdx.x & 127;
         grp = threadIdx.x >> 7;
@@ -372,10 +403,31 @@ struct Kernel {
 
     // combine sources: a TMEM region, the packed product (left + right), a
     // staged operand (hi + lo), each times a coefficient
-    __device__ Src T(uint32_t c_, float k) const { return {SRC_TMEM, c_, 0u, 0, k}; }
-    __device__ Src Pk(float k) const { return {SRC_PAIR, pl, pr, 0, k}; }
-    __device__ Src S(int stage, float k) const { return {SRC_STAGED, 0u, 0u, stage, k}; }
-    __device__ static Src none() { return {SRC_NONE, 0u, 0u, 0, 0.f}; }
+    __device__ static SrcT T(uint32_t c_, float k) { return {c_, k}; }
+    __device__ SrcP Pk(float k) const { return {pl, pr, k}; }
+    __device__ static SrcS S(int stage, float k) { return {stage, k}; }
+    __device__ static SrcN none() { return {0.f}; }
+
+    // Staged operand sg <- a staged image in global memory (npad x 512 bytes:
+    // hi part, then lo part), by one bulk copy.  All threads; no MMA may still
+    // read sg.  Earlier generic accesses to sg (and the generic writes of the
+    // image, fenced by their writers) are ordered before the copy by the proxy
+    // fence and the barrier; wait_bulk() makes the operand usable.
+    __device__ void bulk_load(int sg, const uint8_t* g) {
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) bulk_g2s(st_addr[sg], g, (uint32_t)npad * 512u, mbar_bulk);
+    }
+    __device__ bool wait_bulk() {
+        bool ok = mbar_wait(mbar_bulk, phase_bulk);
+        phase_bulk ^= 1u;
+        if (!ok) {
+            c.abort = 1;
+            set_error(a.err, GB_ERR_TIMEOUT);
+        }
+        __syncthreads();
+        return c.abort == 0;
+    }
 
     // all threads: make generic smem writes and TMEM stores visible to the MMA
     __device__ void sync_for_mma() {
@@ -451,110 +503,132 @@ struct Kernel {
         return wait_mma();
     }
 
-    // 16 columns of row `row` of staged operand sg as FP32 (hi + lo, exact),
-    // in staged units
-    __device__ void load_staged16(int sg, int c0, float (&v)[16]) const {
-        const uint8_t* p0 = st[sg] + elem_off(row, c0);
-        const uint8_t* p1 = st[sg] + elem_off(row, c0 + 8);
-        const uint4 q[4] = {*(const uint4*)p0, *(const uint4*)p1, *(const uint4*)(p0 + lo_off),
-                            *(const uint4*)(p1 + lo_off)};
-        const uint32_t* w = (const uint32_t*)q;
+    // 8 columns [c0, c0 + 8) of row `row` of staged operand sg as FP32 (hi +
+    // lo, exact), in staged units
+    __device__ void load_staged8(int sg, int c0, float (&v)[8]) const {
+        const uint8_t* p = st[sg] + elem_off(row, c0);
+        const uint4 h4 = *(const uint4*)p, l4 = *(const uint4*)(p + lo_off);
+        const uint32_t w[8] = {h4.x, h4.y, h4.z, h4.w, l4.x, l4.y, l4.z, l4.w};
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < 4; ++j) {
             float2 h, l;
             if (fmt == 0) {
                 h = __half22float2(*(const __half2*)&w[j]);
-                l = __half22float2(*(const __half2*)&w[8 + j]);
+                l = __half22float2(*(const __half2*)&w[4 + j]);
             } else {
                 h = __bfloat1622float2(*(const __nv_bfloat162*)&w[j]);
-                l = __bfloat1622float2(*(const __nv_bfloat162*)&w[8 + j]);
+                l = __bfloat1622float2(*(const __nv_bfloat162*)&w[4 + j]);
             }
             v[2 * j] = h.x + l.x;
             v[2 * j + 1] = h.y + l.y;
         }
     }
 
-    // issue the TMEM loads of one source for chunk c0 (no wait)
-    __device__ void src_issue(const Src& q, int c0, uint32_t (&r1)[16], uint32_t (&r2)[16]) const {
-        if (q.kind == SRC_TMEM || q.kind == SRC_PAIR) tmem_ld16_issue(col(q.c) + lane_off + c0, r1);
-        if (q.kind == SRC_PAIR) tmem_ld16_issue(col(q.c2) + lane_off + c0, r2);
+    // issue the TMEM loads of one source for the 8 columns at c0 (no wait)
+    template <class Q>
+    __device__ void src_issue(const Q& q, int c0, uint32_t (&r1)[8], uint32_t (&r2)[8]) const {
+        if constexpr (Q::loads >= 1) tmem_ld8_issue(col(q.c) + lane_off + c0, r1);
+        if constexpr (Q::loads == 2) tmem_ld8_issue(col(q.c2) + lane_off + c0, r2);
     }
 
-    // value of one source for chunk c0 after the wait, times k (target units)
-    __device__ void src_value(const Src& q, float k, int c0, uint32_t (&r1)[16], uint32_t (&r2)[16],
-                              float (&v)[16]) const {
-        if (q.kind == SRC_STAGED) {
-            load_staged16(q.stage, c0, v);
+    // add k x (one source at c0) to v, after the wait
+    template <class Q>
+    __device__ void src_add(const Q& q, float k, int c0, uint32_t (&r1)[8], uint32_t (&r2)[8],
+                            float (&v)[8]) const {
+        if constexpr (Q::staged) {
+            float w[8];
+            load_staged8(q.stage, c0, w);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] *= k;
-            return;
-        }
-        pin16(r1);
-        if (q.kind == SRC_PAIR) {
-            pin16(r2);
+            for (int j = 0; j < 8; ++j) v[j] = fmaf(w[j], k, v[j]);
+        } else if constexpr (Q::loads == 2) {
+            pin8(r1);
+            pin8(r2);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = (__uint_as_float(r1[j]) + __uint_as_float(r2[j])) * k;
-        } else {
+            for (int j = 0; j < 8; ++j) v[j] = fmaf(__uint_as_float(r1[j]) + __uint_as_float(r2[j]), k, v[j]);
+        } else if constexpr (Q::loads == 1) {
+            pin8(r1);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r1[j]) * k;
+            for (int j = 0; j < 8; ++j) v[j] = fmaf(__uint_as_float(r1[j]), k, v[j]);
         }
     }
 
-    // Row-wise combination over this thread's 16-column chunks:
-    //   u = (A + cd I) + B   (A, B: sources with their coefficients; cd on the
-    //   diagonal of the n x n block)
-    // written to the FP32 TMEM region at column `out` (TMEM units; < 0: none),
-    // staged operand `sg` and/or the global FP32 128 x 128 block `gdst`
-    // (values, in column groups of four: element (r, c) at
-    // ((c / 4) * 128 + r) * 4 + c % 4).  Every TMEM region and staged operand
-    // is exactly zero outside the n x n block, so only the identity needs
-    // masking.  The power-of-two unit changes are folded into the coefficients.
-    __device__ void combine(const Src& A, const Src& B, float cd, int out, int sg, float* gdst) {
-        const bool stage_only = out < 0 && gdst == nullptr;
-        const float unit = stage_only ? STAGE_SCALE * TMEM_INV : 1.f;  // TMEM units -> target units
-        const float ka = A.k * (A.kind == SRC_STAGED ? unit * TMEM_SCALE / STAGE_SCALE : unit);
-        const float kb = B.k * (B.kind == SRC_STAGED ? unit * TMEM_SCALE / STAGE_SCALE : unit);
-        const float kd = cd * TMEM_SCALE * unit;
-        const bool diag = cd != 0.f && row < n;
-        for (int ch = ch0; ch < ch1; ++ch) {
-            const int c0 = 16 * ch;
-            uint32_t a1[16], a2[16], b1[16], b2[16];
-            src_issue(A, c0, a1, a2);
-            src_issue(B, c0, b1, b2);
-            const bool tm = A.kind == SRC_TMEM || A.kind == SRC_PAIR || B.kind == SRC_TMEM || B.kind == SRC_PAIR;
-            if (tm) tmem_wait_ld();
-            float u[16];
-            src_value(A, ka, c0, a1, a2, u);
-            if (diag && (unsigned)(row - c0) < 16u) {
+    // TMEM load registers of one 8-column unit (two sources, up to two loads each)
+    struct Regs {
+        uint32_t a1[8], a2[8], b1[8], b2[8];
+    };
+
+    template <class QA, class QB>
+    __device__ __forceinline__ void unit_issue(const QA& A, const QB& B, int u, Regs& r) const {
+        src_issue(A, 8 * u, r.a1, r.a2);
+        src_issue(B, 8 * u, r.b1, r.b2);
+    }
+
+    template <class QA, class QB>
+    __device__ __forceinline__ void unit_body(const QA& A, const QB& B, float ka, float kb, float kd, float ks,
+                                              bool diag, int out, int sg, uint8_t* gst, int u, Regs& r) const {
+        const int c0 = 8 * u;
+        float v[8];
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (c0 + j == row) u[j] += kd;
-            }
-            if (B.kind != SRC_NONE) {
-                float w[16];
-                src_value(B, kb, c0, b1, b2, w);
+        for (int j = 0; j < 8; ++j) v[j] = 0.f;
+        src_add(A, ka, c0, r.a1, r.a2, v);
+        if (diag && (unsigned)(row - c0) < 8u) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) u[j] += w[j];
-            }
-            if (out >= 0) tmem_st16(col((uint32_t)out) + lane_off + c0, u);
+            for (int j = 0; j < 8; ++j)
+                if (c0 + j == row) v[j] += kd;
+        }
+        src_add(B, kb, c0, r.b1, r.b2, v);
+        if (out >= 0) tmem_st8(col((uint32_t)out) + lane_off + c0, v);
+        if (sg >= 0 || gst) {
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) split_pair(v[2 * j] * ks, v[2 * j + 1] * ks, fmt, hi[j], lo[j]);
+            const uint32_t off = elem_off(row, c0);
             if (sg >= 0) {
-                if (stage_only) {
-                    stage_chunk(st[sg], row, c0, u, fmt, lo_off);
-                } else {
-                    float t[16];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) t[j] = u[j] * (STAGE_SCALE * TMEM_INV);
-                    stage_chunk(st[sg], row, c0, t, fmt, lo_off);
-                }
+                uint8_t* p = st[sg] + off;
+                *(uint4*)p = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                *(uint4*)(p + lo_off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
             }
-            if (gdst) {
-#pragma unroll
-                for (int j = 0; j < 16; j += 4)
-                    *(float4*)(gdst + ((size_t)((c0 + j) >> 2) * NMAX + row) * 4) = make_float4(
-                        u[j] * TMEM_INV, u[j + 1] * TMEM_INV, u[j + 2] * TMEM_INV, u[j + 3] * TMEM_INV);
+            if (gst) {
+                uint8_t* p = gst + off;
+                *(uint4*)p = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                *(uint4*)(p + lo_off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
             }
+        }
+    }
+
+    // Row-wise combination u = (A + cd I) + B (A, B: sources with their
+    // coefficients; cd on the diagonal of the n x n block), written to the
+    // FP32 TMEM region at column `out` (TMEM units; < 0: none), staged operand
+    // `sg` and/or a staged image `gst` in global memory (the layout of a staged
+    // operand, npad x 512 bytes; see bulk_load).
+    // Every TMEM region and staged operand is exactly zero outside the n x n
+    // block, so only the identity needs masking.  The power-of-two unit changes
+    // are folded into the coefficients.
+    // Work split: 8-column units, unit u to column group u mod 3 (balanced to
+    // one unit).  One unit's loads per wait: the other warps of the SM
+    // sub-partition cover the load latency (keeping the next unit's loads in
+    // flight measured slower, from the extra live registers).
+    template <class QA, class QB>
+    __device__ __forceinline__ void combine(const QA& A, const QB& B, float cd, int out, int sg, uint8_t* gst) {
+        const bool stage_only = out < 0;
+        const float unit = stage_only ? STAGE_SCALE * TMEM_INV : 1.f;  // TMEM units -> target units
+        const float ka = A.k * (QA::staged ? unit * TMEM_SCALE / STAGE_SCALE : unit);
+        const float kb = B.k * (QB::staged ? unit * TMEM_SCALE / STAGE_SCALE : unit);
+        const float kd = cd * TMEM_SCALE * unit;
+        const float ks = stage_only ? 1.f : STAGE_SCALE * TMEM_INV;  // target units -> staged units
+        const bool diag = cd != 0.f && row < n;
+        constexpr bool tm = QA::loads + QB::loads > 0;
+        const int nu = npad / 8;
+        Regs r0;
+        for (int u = grp; u < nu; u += GROUPS) {
+            if constexpr (tm) {
+                unit_issue(A, B, u, r0);
+                tmem_wait_ld();
+            }
+            unit_body(A, B, ka, kb, kd, ks, diag, out, sg, gst, u, r0);
         }
         if (out >= 0) tmem_wait_st();
+        if (gst) fence_proxy_async_global();  // read back by a bulk copy
     }
 
     // largest k <= kmax with 4^k max_r sum_c |P_rc| <= 1 for the product P
@@ -802,23 +876,6 @@ struct Kernel {
         }
     }
 
-    // staged operand from a global FP32 128 x 128 block in column groups of
-    // four (element (r, c) at ((c / 4) * 128 + r) * 4 + c % 4; coalesced)
-    __device__ void stage_global(const float* g, int sg) {
-        for (int ch = ch0; ch < ch1; ++ch) {
-            float v[16];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 x = *(const float4*)(g + ((size_t)(4 * ch + q) * NMAX + row) * 4);
-                v[4 * q] = x.x * STAGE_SCALE;
-                v[4 * q + 1] = x.y * STAGE_SCALE;
-                v[4 * q + 2] = x.z * STAGE_SCALE;
-                v[4 * q + 3] = x.w * STAGE_SCALE;
-            }
-            stage_chunk(st[sg], row, c0_of(ch), v, fmt, lo_off);
-        }
-    }
-
     // staged operand from a gathered block beta M (FP32, column groups of four):
     // scale x blk, scale = 2^-(s+1) [x sigma] (exact power of two), and, with
     // use_diag, the diagonal dscale x c.dg (the x0 diagonal computed in FP64)
@@ -864,6 +921,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
     if (threadIdx.x == 0) {
         c.abort = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(K.mbar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(K.mbar_bulk) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (threadIdx.x < 32) {
@@ -907,7 +965,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
         if (K.grp == 0)
             c.dg[K.row] = K.row < n ? (float)(ldexp(a.beta, -(s + 1)) * (a.hdiag[s0 + K.row] - a.mu)) : 0.f;
         __syncthreads();
-        float* z1base = a.z1pool + (size_t)i * (a.m > 0 ? a.m : 1) * NMAX * NMAX;
+        // the response state Z1 of the subgraph in flight: this CTA's scratch
+        // (rewritten every step, so it stays in L2)
+        uint8_t* z1base = (uint8_t*)(a.z1pool + (size_t)blockIdx.x * (a.m > 0 ? a.m : 1) * NMAX * NMAX);
 
         // ---- Taylor start: Q = x0^2, T = I - Q/3 + 2 Q^2/15 (X region: Q, Z region: T) ----
         const float* hb = a.hblk + a.boff[i];
@@ -941,7 +1001,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
             K.combine(K.T(K.zc, 1.f), K.none(), 0.f, -1, 2, nullptr);      // S2 = T
             K.stage_dense(h1b, x1scale, false, 0.f, 1);                   // S1 = X1
             if (!(ok = K.gemm(1, 2, true))) break;                         // P += X1 T
-            K.combine(K.Pk(1.f), K.none(), 0.f, -1, -1, z1base + (size_t)r * NMAX * NMAX);
+            K.combine(K.Pk(1.f), K.none(), 0.f, -1, -1, z1base + (size_t)r * STAGE_BYTES);
         }
         if (!ok) break;
         K.combine(K.T(K.zc, 1.f), K.none(), 0.f, -1, 2, nullptr);          // S2 = T
@@ -957,10 +1017,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
             if (!(ok = K.gemm(1, 1, false, true))) break;                          // P = Y^2 (hi parts)
             K.combine(K.S(1, -80.f / 99.f), K.T(K.pl, 32.f / 99.f), 98.f / 99.f, K.xc, 2, nullptr);  // X0
             for (int j = 0; j < a.ns_iters && ok; ++j) {
+                // Before the last correction X R only needs a few digits: |R| is
+                // about 1e-2 after the Chebyshev start, so the hi parts alone leave
+                // an error ~2^-11 |R| in X, which the next correction squares.
+                const bool rough = j + 1 < a.ns_iters;
                 if (!(ok = K.gemm(1, 2))) break;                                   // P = Y X
+                if (a.m > 0 && !last && j + 1 == a.ns_iters) K.bulk_load(1, z1base);  // S1 <- Z1 (Y done)
                 K.combine(K.T(K.xc, -1.f), K.Pk(-1.f), 1.f, -1, 0, nullptr);       // S0 = R = (I - X) - Y X
-                if (!(ok = K.gemm(2, 0))) break;                                   // P = X R
-                K.combine(K.T(K.xc, 1.f), K.Pk(1.f), 0.f, K.xc, 2, nullptr);       // X += X R, S2 = X
+                if (!(ok = K.gemm(2, 0, false, rough))) break;                     // P = X R
+                if (rough) K.combine(K.T(K.xc, 1.f), K.T(K.pl, 1.f), 0.f, K.xc, 2, nullptr);     // X += X R, S2 = X
+                else K.combine(K.T(K.xc, 1.f), K.Pk(1.f), 0.f, K.xc, 2, nullptr);
             }
             if (!ok) break;
             if (last) {
@@ -986,8 +1052,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
             }
             for (int r = 0; r < a.m && ok; ++r) {
                 // Z1 <- 2 X Z1 X - (W Z1 / 2) W
-                float* z1 = z1base + (size_t)r * NMAX * NMAX;
-                K.stage_global(z1, 1);                                             // S1 = Z1
+                uint8_t* z1 = z1base + (size_t)r * STAGE_BYTES;
+                if (r > 0 || last || a.ns_iters < 1) K.bulk_load(1, z1);          // S1 <- Z1
+                if (!(ok = K.wait_bulk())) break;                                  // S1 = Z1
                 if (!(ok = K.gemm(2, 1))) break;                                   // P = X Z1
                 K.combine(K.Pk(2.f), K.none(), 0.f, K.xc, -1, nullptr);            // X region = 2 X Z1
                 if (!(ok = K.gemm(0, 1))) break;                                   // P = W Z1
@@ -1118,7 +1185,8 @@ int launch_split_pass(gb_handle* h, const PassArgs& a) {
     }
     int sms = 0;
     GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-    const int grid = a.n_sub < sms ? a.n_sub : sms;
+    int grid = a.n_sub < sms ? a.n_sub : sms;
+    if (grid > GB_SPLIT_MAX_CTAS) grid = GB_SPLIT_MAX_CTAS;
     GB_LAUNCH(h, k_fermi_split, grid, THREADS, SMEM_BYTES, a);
     return GB_OK;
 }
