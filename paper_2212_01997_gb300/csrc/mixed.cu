@@ -28,13 +28,17 @@
 // swizzle: element (r, k) of the hi part at byte
 // (k/8)*2048 + (r/8)*128 + (r%8)*16 + (k%8)*2, the lo part npad*256 bytes on.
 //
-// The per-step schedule (Z FP32 in TMEM):
-//   stage Z -> S0;  P = Z Z;  stage Y -> S1;  P = Y Y (hi parts: it only seeds
-//   Newton-Schulz);  X0 = (98 I - 80 Y + 32 Y^2)/99 -> X and S2;
-//   repeat: P = Y X; stage R = (I - X) - P -> S0; P = X R; X += P -> X, S2;
-//   stage Z -> S0; P = W/2 = X Z; Z = 2 P (next step), stage W -> S0;
-//   per RHS: stage Z1 -> S1; P = X Z1 -> X region (x2); P = W Z1 -> S1 (x -1/2);
-//            P = (-W Z1 / 2) W; stage 2 X Z1 -> S1; P += (2 X Z1) X -> global FP32
+// The per-step schedule (Z FP32 in TMEM, staged in S0 on entry):
+//   P = Z Z;  stage Y -> S1;  P = Y Y (hi parts: it only seeds Newton-Schulz);
+//   X0 = (98 I - 80 Y + 32 Y^2)/99 -> X and S2;
+//   first correction: P = Y X; R = (I - X) - P, hi parts -> lo half of S2;
+//     P = X_hi R_hi; X += P -> X, S2;
+//   last correction: P = Y X; stage R -> S1 (S0 in the last step, which still
+//     needs Y); P = X R; X += P -> X, S2;
+//   P = W/2 = X Z; Z = 2 P (next step) -> Z region and S0;
+//   per RHS: S1 <- Z1 (bulk copy of its staged image); P = X Z1 -> X region
+//            (x2); P = W Z1 -> S1 (x -1/2); P = (-W Z1 / 2) W; stage 2 X Z1 ->
+//            S1; P += (2 X Z1) X -> staged image of Z1 in global memory
 //            (last step: only its core columns, as d1_lambda).
 // The last step also forms d1_mu = beta ((I - Y) X)^2 / 4 and redoes Z_s on
 // the core columns on the CUDA cores (see refine_core).
@@ -258,6 +262,16 @@ __device__ __forceinline__ void split_pair(float x0, float x1, int fmt, uint32_t
     }
 }
 
+// hi parts of a pair (rn), packed
+__device__ __forceinline__ uint32_t hi_pair(float x0, float x1, int fmt) {
+    if (fmt == 0) {
+        const __half2 h = __floats2half2_rn(x0, x1);
+        return *(const uint32_t*)&h;
+    }
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    return *(const uint32_t*)&h;
+}
+
 // write 16 consecutive columns [c0, c0+16) of row r into a staged operand
 // (hi part at the layout offset, lo part lo_off bytes further)
 __device__ __forceinline__ void stage_chunk(uint8_t* stage, int r, int c0, const float* v, int fmt, uint32_t lo_off) {
@@ -349,8 +363,8 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
 struct Kernel {
     const PassArgs& a;
     Ctl& c;
-    uint8_t* st[NSTAGE];
-    uint32_t st_addr[NSTAGE];
+    uint8_t* st0;        // staged operand k at st0 + k STAGE_BYTES (no array:
+    uint32_t st_addr0;   // a runtime slot index would move it to local memory)
     uint32_t tbase;
     uint32_t mbar;
     uint32_t phase;
@@ -366,10 +380,8 @@ struct Kernel {
     uint32_t zc, xc, pl, pr;  // TMEM columns: Z, X (FP32 state), product left / right halves
 
     __device__ Kernel(const PassArgs& a_, Ctl& c_, uint8_t* smem) : a(a_), c(c_) {
-        for (int k = 0; k < NSTAGE; ++k) {
-            st[k] = smem + k * STAGE_BYTES;
-            st_addr[k] = smem_u32(st[k]);
-        }
+        st0 = smem;
+        st_addr0 = smem_u32(smem);
         mbar = smem_u32(&c.mbar);
         phase = 0;
         mbar_bulk = smem_u32(&c.mbar_bulk);
@@ -399,6 +411,8 @@ struct Kernel {
     }
 
     __device__ uint32_t col(uint32_t cidx) const { return tbase + cidx; }
+    __device__ uint8_t* st(int k) const { return st0 + (uint32_t)k * STAGE_BYTES; }
+    __device__ uint32_t sa_of(int k) const { return st_addr0 + (uint32_t)k * STAGE_BYTES; }
     __device__ static int c0_of(int ch) { return ch * 16; }
 
     // combine sources: a TMEM region, the packed product (left + right), a
@@ -416,7 +430,7 @@ struct Kernel {
     __device__ void bulk_load(int sg, const uint8_t* g) {
         fence_proxy_async();
         __syncthreads();
-        if (threadIdx.x == 0) bulk_g2s(st_addr[sg], g, (uint32_t)npad * 512u, mbar_bulk);
+        if (threadIdx.x == 0) bulk_g2s(sa_of(sg), g, (uint32_t)npad * 512u, mbar_bulk);
     }
     __device__ bool wait_bulk() {
         bool ok = mbar_wait(mbar_bulk, phase_bulk);
@@ -437,10 +451,10 @@ struct Kernel {
     }
 
     __device__ uint64_t da(int sa, uint32_t part, int ks) const {
-        return make_desc(st_addr[sa] + part + (uint32_t)ks * 2u * LBO);   // A: 16 columns of K
+        return make_desc(sa_of(sa) + part + (uint32_t)ks * 2u * LBO);   // A: 16 columns of K
     }
     __device__ uint64_t db(int sb, uint32_t part, int ks) const {
-        return make_desc_b(st_addr[sb] + part + (uint32_t)ks * 2u * SBO); // B: 16 rows of K
+        return make_desc_b(sa_of(sb) + part + (uint32_t)ks * 2u * SBO); // B: 16 rows of K
     }
 
     // P = A B (acc = false) or P += A B, split in FP16 parts, per K step:
@@ -460,10 +474,12 @@ struct Kernel {
     }
 
     // left = A_hi B_hi only (a product that only seeds an iteration)
-    __device__ void issue_hh(int sa, int sb) {
+    // (B's hi part read from byte offset bpart of slot sb: lo_off for a hi part
+    // parked in a slot's lo half)
+    __device__ void issue_hh(int sa, int sb, uint32_t bpart) {
         const int K = npad / 16;
         const uint32_t id1 = make_idesc(fmt, 0, npad);
-        for (int ks = 0; ks < K; ++ks) mma_f16(col(pl), da(sa, 0, ks), db(sb, 0, ks), id1, ks > 0 ? 1u : 0u);
+        for (int ks = 0; ks < K; ++ks) mma_f16(col(pl), da(sa, 0, ks), db(sb, bpart, ks), id1, ks > 0 ? 1u : 0u);
     }
 
     // wait for every MMA issued so far by thread 0
@@ -482,11 +498,11 @@ struct Kernel {
 
     // one product P = A B (P += A B with acc; hi parts only with hh) of
     // staged operands sa, sb
-    __device__ bool gemm(int sa, int sb, bool acc = false, bool hh = false) {
+    __device__ bool gemm(int sa, int sb, bool acc = false, bool hh = false, uint32_t bpart = 0) {
         sync_for_mma();
         if (threadIdx.x == 0) {
             fence_after();
-            if (hh) issue_hh(sa, sb);
+            if (hh) issue_hh(sa, sb, bpart);
             else issue_prod(sa, sb, acc);
         }
         return wait_mma();
@@ -506,7 +522,7 @@ struct Kernel {
     // 8 columns [c0, c0 + 8) of row `row` of staged operand sg as FP32 (hi +
     // lo, exact), in staged units
     __device__ void load_staged8(int sg, int c0, float (&v)[8]) const {
-        const uint8_t* p = st[sg] + elem_off(row, c0);
+        const uint8_t* p = st(sg) + elem_off(row, c0);
         const uint4 h4 = *(const uint4*)p, l4 = *(const uint4*)(p + lo_off);
         const uint32_t w[8] = {h4.x, h4.y, h4.z, h4.w, l4.x, l4.y, l4.z, l4.w};
 #pragma unroll
@@ -565,7 +581,8 @@ struct Kernel {
 
     template <class QA, class QB>
     __device__ __forceinline__ void unit_body(const QA& A, const QB& B, float ka, float kb, float kd, float ks,
-                                              bool diag, int out, int sg, uint8_t* gst, int u, Regs& r) const {
+                                              bool diag, int out, int sg, uint8_t* gst, int shl, int u,
+                                              Regs& r) const {
         const int c0 = 8 * u;
         float v[8];
 #pragma unroll
@@ -578,13 +595,19 @@ struct Kernel {
         }
         src_add(B, kb, c0, r.b1, r.b2, v);
         if (out >= 0) tmem_st8(col((uint32_t)out) + lane_off + c0, v);
+        if (shl >= 0) {
+            uint32_t hi[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) hi[j] = hi_pair(v[2 * j] * ks, v[2 * j + 1] * ks, fmt);
+            *(uint4*)(st(shl) + lo_off + elem_off(row, c0)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        }
         if (sg >= 0 || gst) {
             uint32_t hi[4], lo[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) split_pair(v[2 * j] * ks, v[2 * j + 1] * ks, fmt, hi[j], lo[j]);
             const uint32_t off = elem_off(row, c0);
             if (sg >= 0) {
-                uint8_t* p = st[sg] + off;
+                uint8_t* p = st(sg) + off;
                 *(uint4*)p = make_uint4(hi[0], hi[1], hi[2], hi[3]);
                 *(uint4*)(p + lo_off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
             }
@@ -600,7 +623,9 @@ struct Kernel {
     // coefficients; cd on the diagonal of the n x n block), written to the
     // FP32 TMEM region at column `out` (TMEM units; < 0: none), staged operand
     // `sg` and/or a staged image `gst` in global memory (the layout of a staged
-    // operand, npad x 512 bytes; see bulk_load).
+    // operand, npad x 512 bytes; see bulk_load).  With shl >= 0, the hi parts
+    // alone go to the lo half of staged operand shl (an operand only a product
+    // of hi parts reads; see issue_hh).
     // Every TMEM region and staged operand is exactly zero outside the n x n
     // block, so only the identity needs masking.  The power-of-two unit changes
     // are folded into the coefficients.
@@ -609,7 +634,8 @@ struct Kernel {
     // sub-partition cover the load latency (keeping the next unit's loads in
     // flight measured slower, from the extra live registers).
     template <class QA, class QB>
-    __device__ __forceinline__ void combine(const QA& A, const QB& B, float cd, int out, int sg, uint8_t* gst) {
+    __device__ __forceinline__ void combine(const QA& A, const QB& B, float cd, int out, int sg, uint8_t* gst,
+                                            int shl = -1) {
         const bool stage_only = out < 0;
         const float unit = stage_only ? STAGE_SCALE * TMEM_INV : 1.f;  // TMEM units -> target units
         const float ka = A.k * (QA::staged ? unit * TMEM_SCALE / STAGE_SCALE : unit);
@@ -625,7 +651,7 @@ struct Kernel {
                 unit_issue(A, B, u, r0);
                 tmem_wait_ld();
             }
-            unit_body(A, B, ka, kb, kd, ks, diag, out, sg, gst, u, r0);
+            unit_body(A, B, ka, kb, kd, ks, diag, out, sg, gst, shl, u, r0);
         }
         if (out >= 0) tmem_wait_st();
         if (gst) fence_proxy_async_global();  // read back by a bulk copy
@@ -728,7 +754,7 @@ struct Kernel {
     template <int NC>
     __device__ void refine_core(uint32_t zs, uint32_t xs, float zsc, int ncore) {
         constexpr int VL = NC + 4;
-        float* Vz = (float*)st[0];
+        float* Vz = (float*)st(0);
         float* Vw = Vz + NMAX * VL;
         float* Vt = Vw + NMAX * VL;
         FF* Wd = (FF*)(Vt + NMAX * VL);  // [NC][NMAX]
@@ -904,7 +930,7 @@ struct Kernel {
                 for (int j = 0; j < 16; ++j)
                     if (c0 + j == row) v[j] = dv;
             }
-            stage_chunk(st[sg], row, c0, v, fmt, lo_off);
+            stage_chunk(st(sg), row, c0, v, fmt, lo_off);
         }
     }
 };
@@ -1006,12 +1032,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
         if (!ok) break;
         K.combine(K.T(K.zc, 1.f), K.none(), 0.f, -1, 2, nullptr);          // S2 = T
         if (!K.gemm(0, 2)) break;                                         // P = Z0 = x0 T
-        K.combine(K.Pk(1.f), K.none(), 0.f, K.zc, -1, nullptr);            // Z region = Z0
+        K.combine(K.Pk(1.f), K.none(), 0.f, K.zc, 0, nullptr);             // Z region = Z0, S0 = Z0
 
         // ---- doublings: Z <- 2 X Z, X = (I + Z^2)^-1 ----
         for (int step = 0; step < s && ok; ++step) {
             const bool last = step == s - 1;
-            K.combine(K.T(K.zc, 1.f), K.none(), 0.f, -1, 0, nullptr);              // S0 = Z
+            // S0 = Z on entry (staged with the Z region by the previous step)
             if (!(ok = K.gemm(0, 0))) break;                                       // P = Y = Z^2
             K.combine(K.Pk(1.f), K.none(), 0.f, -1, 1, nullptr);                   // S1 = Y
             if (!(ok = K.gemm(1, 1, false, true))) break;                          // P = Y^2 (hi parts)
@@ -1022,9 +1048,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
                 // an error ~2^-11 |R| in X, which the next correction squares.
                 const bool rough = j + 1 < a.ns_iters;
                 if (!(ok = K.gemm(1, 2))) break;                                   // P = Y X
-                if (a.m > 0 && !last && j + 1 == a.ns_iters) K.bulk_load(1, z1base);  // S1 <- Z1 (Y done)
-                K.combine(K.T(K.xc, -1.f), K.Pk(-1.f), 1.f, -1, 0, nullptr);       // S0 = R = (I - X) - Y X
-                if (!(ok = K.gemm(2, 0, false, rough))) break;                     // P = X R
+                if (rough) {
+                    // R_hi alone, parked in the lo half of S2 (X_hi R_hi reads
+                    // neither X_lo nor R_lo): S0 keeps Z
+                    K.combine(K.T(K.xc, -1.f), K.Pk(-1.f), 1.f, -1, -1, nullptr, 2);  // R = (I - X) - Y X
+                    if (!(ok = K.gemm(2, 2, false, true, K.lo_off))) break;          // P = X_hi R_hi
+                } else {
+                    // the last correction: R where Y was (Y is done) except in
+                    // the last step, which still needs Y
+                    const int sr = last ? 0 : 1;
+                    K.combine(K.T(K.xc, -1.f), K.Pk(-1.f), 1.f, -1, sr, nullptr);  // S_sr = R
+                    if (!(ok = K.gemm(2, sr))) break;                              // P = X R
+                    if (sr == 1 && a.m > 0) K.bulk_load(1, z1base);                // S1 <- Z1 (R done)
+                }
                 if (rough) K.combine(K.T(K.xc, 1.f), K.T(K.pl, 1.f), 0.f, K.xc, 2, nullptr);     // X += X R, S2 = X
                 else K.combine(K.T(K.xc, 1.f), K.Pk(1.f), 0.f, K.xc, 2, nullptr);
             }
@@ -1040,7 +1076,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
                                0.25f * TMEM_INV);                                  // d1_mu = beta G^2 / 4
                 K.diag_max();
             }
-            K.combine(K.T(K.zc, 1.f), K.none(), 0.f, -1, 0, nullptr);              // S0 = Z
+            if (last || a.ns_iters < 1) K.combine(K.T(K.zc, 1.f), K.none(), 0.f, -1, 0, nullptr);  // S0 = Z
             if (!(ok = K.gemm(2, 0))) break;                                       // P = W / 2 = X Z
             if (last) {
                 // ---- the last doubling redone on the core columns (CUDA cores) ----
@@ -1048,7 +1084,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
                 else K.refine_core<16>(K.zc, K.xc, TMEM_INV, ncore);
                 if (a.m > 0) K.combine(K.Pk(2.f), K.none(), 0.f, -1, 0, nullptr);  // S0 = W
             } else {
-                K.combine(K.Pk(2.f), K.none(), 0.f, K.zc, a.m > 0 ? 0 : -1, nullptr);  // Z region = W (next Z), S0 = W
+                K.combine(K.Pk(2.f), K.none(), 0.f, K.zc, 0, nullptr);             // Z region = W (next Z), S0 = W
             }
             for (int r = 0; r < a.m && ok; ++r) {
                 // Z1 <- 2 X Z1 X - (W Z1 / 2) W
