@@ -29,8 +29,8 @@
 // (k/8)*2048 + (r/8)*128 + (r%8)*16 + (k%8)*2, the lo part npad*256 bytes on.
 //
 // The per-step schedule (Z FP32 in TMEM, staged in S0 on entry):
-//   P = Z Z;  stage Y -> S1;  P = Y Y (hi parts: it only seeds Newton-Schulz);
-//   X0 = (98 I - 80 Y + 32 Y^2)/99 -> X and S2;
+//   P = Z Z;  stage Y -> S1;  X region = Y Y (hi parts: it only seeds
+//   Newton-Schulz);  X0 = (98 I - 80 Y + 32 Y^2)/99 -> X and S2;
 //   first correction: P = Y X; R = (I - X) - P, hi parts -> lo half of S2;
 //     P = X_hi R_hi; X += P -> X, S2;
 //   last correction: P = Y X; stage R -> S1 (S0 in the last step, which still
@@ -245,20 +245,24 @@ __device__ __forceinline__ uint32_t elem_off(int r, int k) {
     return (uint32_t)(k >> 3) * LBO + (uint32_t)(r >> 3) * SBO + (uint32_t)(r & 7) * 16u + (uint32_t)(k & 7) * 2u;
 }
 
-// hi/lo split of a pair of values with packed conversions
+// hi/lo split of a pair of values: hi = rn(x), lo = rn(x - hi), packed.
+// x - hi (exact) comes from one mixed-precision FMA per value, hi x (-1) + x
+// with the 16-bit hi operand read directly, instead of a conversion back to
+// FP32 and a subtraction.
 __device__ __forceinline__ void split_pair(float x0, float x1, int fmt, uint32_t& hi, uint32_t& lo) {
+    float d0, d1;
     if (fmt == 0) {
-        const __half2 h = __floats2half2_rn(x0, x1);
-        const float2 f = __half22float2(h);
-        const __half2 l = __floats2half2_rn(x0 - f.x, x1 - f.y);
-        hi = *(const uint32_t*)&h;
-        lo = *(const uint32_t*)&l;
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(x1), "f"(x0));
+        asm("{.reg .b16 l, h, m;\n mov.b32 {l, h}, %2;\n mov.b16 m, 0xBC00;\n"
+            " fma.rn.f32.f16 %0, l, m, %3;\n fma.rn.f32.f16 %1, h, m, %4;}"
+            : "=f"(d0), "=f"(d1) : "r"(hi), "f"(x0), "f"(x1));
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(d1), "f"(d0));
     } else {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-        const float2 f = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - f.x, x1 - f.y);
-        hi = *(const uint32_t*)&h;
-        lo = *(const uint32_t*)&l;
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(x1), "f"(x0));
+        asm("{.reg .b16 l, h, m;\n mov.b32 {l, h}, %2;\n mov.b16 m, 0xBF80;\n"
+            " fma.rn.f32.bf16 %0, l, m, %3;\n fma.rn.f32.bf16 %1, h, m, %4;}"
+            : "=f"(d0), "=f"(d1) : "r"(hi), "f"(x0), "f"(x1));
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(d1), "f"(d0));
     }
 }
 
@@ -476,10 +480,11 @@ struct Kernel {
     // left = A_hi B_hi only (a product that only seeds an iteration)
     // (B's hi part read from byte offset bpart of slot sb: lo_off for a hi part
     // parked in a slot's lo half)
-    __device__ void issue_hh(int sa, int sb, uint32_t bpart) {
+    // into TMEM columns dc (the left half of P unless given)
+    __device__ void issue_hh(int sa, int sb, uint32_t bpart, uint32_t dc) {
         const int K = npad / 16;
         const uint32_t id1 = make_idesc(fmt, 0, npad);
-        for (int ks = 0; ks < K; ++ks) mma_f16(col(pl), da(sa, 0, ks), db(sb, bpart, ks), id1, ks > 0 ? 1u : 0u);
+        for (int ks = 0; ks < K; ++ks) mma_f16(col(dc), da(sa, 0, ks), db(sb, bpart, ks), id1, ks > 0 ? 1u : 0u);
     }
 
     // wait for every MMA issued so far by thread 0
@@ -498,11 +503,12 @@ struct Kernel {
 
     // one product P = A B (P += A B with acc; hi parts only with hh) of
     // staged operands sa, sb
-    __device__ bool gemm(int sa, int sb, bool acc = false, bool hh = false, uint32_t bpart = 0) {
+    __device__ bool gemm(int sa, int sb, bool acc = false, bool hh = false, uint32_t bpart = 0,
+                         int dc = -1) {
         sync_for_mma();
         if (threadIdx.x == 0) {
             fence_after();
-            if (hh) issue_hh(sa, sb, bpart);
+            if (hh) issue_hh(sa, sb, bpart, dc >= 0 ? (uint32_t)dc : pl);
             else issue_prod(sa, sb, acc);
         }
         return wait_mma();
@@ -1040,8 +1046,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
             // S0 = Z on entry (staged with the Z region by the previous step)
             if (!(ok = K.gemm(0, 0))) break;                                       // P = Y = Z^2
             K.combine(K.Pk(1.f), K.none(), 0.f, -1, 1, nullptr);                   // S1 = Y
-            if (!(ok = K.gemm(1, 1, false, true))) break;                          // P = Y^2 (hi parts)
-            K.combine(K.S(1, -80.f / 99.f), K.T(K.pl, 32.f / 99.f), 98.f / 99.f, K.xc, 2, nullptr);  // X0
+            // Y^2 (hi parts: it only seeds Newton-Schulz) into the X region, so P keeps Y
+            if (!(ok = K.gemm(1, 1, false, true, 0, (int)K.xc))) break;
+            K.combine(K.Pk(-80.f / 99.f), K.T(K.xc, 32.f / 99.f), 98.f / 99.f, K.xc, 2, nullptr);  // X0
             for (int j = 0; j < a.ns_iters && ok; ++j) {
                 // Before the last correction X R only needs a few digits: |R| is
                 // about 1e-2 after the Chebyshev start, so the hi parts alone leave
