@@ -168,25 +168,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
     return false;
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-        "%12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
-                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]),
-                   "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
-                 :
-                 : "memory");
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-}
-
 // waits for every tcgen05.ld this thread issued
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -274,20 +255,6 @@ __device__ __forceinline__ uint32_t hi_pair(float x0, float x1, int fmt) {
     }
     const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
     return *(const uint32_t*)&h;
-}
-
-// write 16 consecutive columns [c0, c0+16) of row r into a staged operand
-// (hi part at the layout offset, lo part lo_off bytes further)
-__device__ __forceinline__ void stage_chunk(uint8_t* stage, int r, int c0, const float* v, int fmt, uint32_t lo_off) {
-    uint32_t hi[8], lo[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) split_pair(v[2 * j], v[2 * j + 1], fmt, hi[j], lo[j]);
-    uint8_t* p0 = stage + elem_off(r, c0);
-    uint8_t* p1 = stage + elem_off(r, c0 + 8);
-    *(uint4*)p0 = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-    *(uint4*)p1 = make_uint4(hi[4], hi[5], hi[6], hi[7]);
-    *(uint4*)(p0 + lo_off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-    *(uint4*)(p1 + lo_off) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
 }
 
 // float -> double by integer operations (exact; FP32 subnormals flush to
@@ -417,7 +384,6 @@ struct Kernel {
     __device__ uint32_t col(uint32_t cidx) const { return tbase + cidx; }
     __device__ uint8_t* st(int k) const { return st0 + (uint32_t)k * STAGE_BYTES; }
     __device__ uint32_t sa_of(int k) const { return st_addr0 + (uint32_t)k * STAGE_BYTES; }
-    __device__ static int c0_of(int ch) { return ch * 16; }
 
     // combine sources: a TMEM region, the packed product (left + right), a
     // staged operand (hi + lo), each times a coefficient
@@ -696,29 +662,33 @@ struct Kernel {
     }
 
     // Matrix times NC vectors on the CUDA cores: P_g[cc][row] = sum over this
-    // column group's k of M_row,k v[k][cc], M = scale x TMEM slot sl.  v is in
-    // shared memory as [k][NC + 4] floats (broadcast float4 reads); FP32
-    // products are summed per 16-column chunk (round to nearest), the chunk
-    // sums without rounding error (float pairs).  P holds the column groups'
-    // partials as float pairs, [GROUPS][NC][NMAX] (column-major, so the
-    // row-indexed stores are conflict-free); the caller adds them after a
-    // barrier.
+    // column group's k of M_row,k v[k][cc], M = scale x TMEM slot sl (scale a
+    // power of two, applied to the sums: exact).  v is in shared memory as
+    // [k][NC + 4] floats (broadcast float4 reads); FP32 products are summed
+    // per 8-column unit (round to nearest; units dealt to the column groups as
+    // in combine), the unit sums without rounding error (float pairs).  P
+    // holds the column groups' partials as float pairs, [GROUPS][NC][NMAX]
+    // (column-major, so the row-indexed stores are conflict-free); the caller
+    // adds them after a barrier.
     template <int NC>
     __device__ void rowvec(uint32_t sl, float scale, const float* v, FF* P) {
         constexpr int VL = NC + 4;
-        float hi[NC], lo[NC];  // chunk sums accumulated as unevaluated float pairs
+        float hi[NC], lo[NC];  // unit sums accumulated as unevaluated float pairs
 #pragma unroll
         for (int cc = 0; cc < NC; ++cc) hi[cc] = lo[cc] = 0.f;
-        for (int ch = ch0; ch < ch1; ++ch) {
-            const int c0 = ch * 16;
-            float m[16];
-            tmem_ld16(col(sl) + lane_off + c0, m);
+        const int nu = npad / 8;
+        for (int u = grp; u < nu; u += GROUPS) {
+            const int c0 = u * 8;
+            uint32_t m[8];
+            tmem_ld8_issue(col(sl) + lane_off + c0, m);
+            tmem_wait_ld();
+            pin8(m);
             float acc[NC];
 #pragma unroll
             for (int cc = 0; cc < NC; ++cc) acc[cc] = 0.f;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float mj = m[j] * scale;
+            for (int j = 0; j < 8; ++j) {
+                const float mj = __uint_as_float(m[j]);
                 const float4* vr = (const float4*)(v + (c0 + j) * VL);
 #pragma unroll
                 for (int q = 0; q < NC / 4; ++q) {
@@ -738,7 +708,10 @@ struct Kernel {
         }
         FF* Pg = P + grp * (NC * NMAX);
 #pragma unroll
-        for (int cc = 0; cc < NC; ++cc) Pg[cc * NMAX + row] = two_sum(hi[cc], lo[cc]);
+        for (int cc = 0; cc < NC; ++cc) {
+            const FF t = two_sum(hi[cc], lo[cc]);
+            Pg[cc * NMAX + row] = FF{t.hi * scale, t.lo * scale};
+        }
     }
 
     // row `row` of NC float vectors, [row][NC + 4] (16-byte stores, conflict-free)
@@ -911,32 +884,43 @@ struct Kernel {
     // staged operand from a gathered block beta M (FP32, column groups of four):
     // scale x blk, scale = 2^-(s+1) [x sigma] (exact power of two), and, with
     // use_diag, the diagonal dscale x c.dg (the x0 diagonal computed in FP64)
+    // 8-column units as in combine (unit u to column group u mod 3); all of a
+    // thread's global loads are issued before the first conversion.
     __device__ void stage_dense(const float* blk, float scale, bool use_diag, float dscale, int sg) {
+        constexpr int MAXU = (NMAX / 8 + GROUPS - 1) / GROUPS;
         const float k = scale * STAGE_SCALE;
         const bool has_diag = use_diag && row < n;
         const float dv = has_diag ? c.dg[row] * dscale * STAGE_SCALE : 0.f;
-        for (int ch = ch0; ch < ch1; ++ch) {
-            const int c0 = c0_of(ch);
-            float v[16];
-            if (row < npad) {
+        const int nu = npad / 8;
+        float4 x[MAXU][2];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 x = *(const float4*)(blk + ((size_t)(4 * ch + q) * npad + row) * 4);
-                    v[4 * q] = x.x * k;
-                    v[4 * q + 1] = x.y * k;
-                    v[4 * q + 2] = x.z * k;
-                    v[4 * q + 3] = x.w * k;
-                }
+        for (int i = 0; i < MAXU; ++i) {
+            const int u = grp + GROUPS * i;
+            if (u < nu && row < npad) {
+                x[i][0] = *(const float4*)(blk + ((size_t)(2 * u) * npad + row) * 4);
+                x[i][1] = *(const float4*)(blk + ((size_t)(2 * u + 1) * npad + row) * 4);
             } else {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = 0.f;
+                x[i][0] = x[i][1] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            if (has_diag && (unsigned)(row - c0) < 16u) {
+        }
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
+        for (int i = 0; i < MAXU; ++i) {
+            const int u = grp + GROUPS * i;
+            if (u >= nu) break;
+            const int c0 = 8 * u;
+            float v[8] = {x[i][0].x * k, x[i][0].y * k, x[i][0].z * k, x[i][0].w * k,
+                          x[i][1].x * k, x[i][1].y * k, x[i][1].z * k, x[i][1].w * k};
+            if (has_diag && (unsigned)(row - c0) < 8u) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
                     if (c0 + j == row) v[j] = dv;
             }
-            stage_chunk(st(sg), row, c0, v, fmt, lo_off);
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) split_pair(v[2 * j], v[2 * j + 1], fmt, hi[j], lo[j]);
+            uint8_t* p = st(sg) + elem_off(row, c0);
+            *(uint4*)p = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *(uint4*)(p + lo_off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
     }
 };
