@@ -8,26 +8,34 @@
 
 // Returns the number of set bits among words[0..W) to every thread.  When
 // `out` is non-null, writes the indices of the set bits in ascending order to
-// out[0..count).  `scan` is shared scratch of blockDim.x int64 values.
+// out[0..count).  `scan` is shared scratch of blockDim.x int64 values (one
+// per warp is used).  Thread t owns a contiguous run of words; the per-thread
+// counts are scanned within each warp by shuffles and across warps through
+// `scan`: two barriers per call.  blockDim.x must be a multiple of 32.
 __device__ inline int64_t bitmap_compact(const uint32_t* words, int W, int32_t* out, int64_t* scan) {
     const int t = threadIdx.x;
     const int nt = blockDim.x;
+    const int lane = t & 31, wid = t >> 5, nw = nt >> 5;
     const int chunk = (W + nt - 1) / nt;
     const int w0 = min(W, t * chunk);
     const int w1 = min(W, w0 + chunk);
-    int64_t local = 0;
+    int local = 0;
     for (int w = w0; w < w1; ++w) local += __popc(words[w]);
-    scan[t] = local;
-    __syncthreads();
-    for (int o = 1; o < nt; o <<= 1) {
-        int64_t x = t >= o ? scan[t - o] : 0;
-        __syncthreads();
-        scan[t] += x;
-        __syncthreads();
+    int incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
     }
-    const int64_t total = scan[nt - 1];
+    if (lane == 31) scan[wid] = incl;
+    __syncthreads();
+    int64_t base = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+        const int64_t v = scan[w];
+        base += w < wid ? v : 0;
+        total += v;
+    }
     if (out) {
-        int64_t pos = scan[t] - local;
+        int64_t pos = base + incl - local;
         for (int w = w0; w < w1; ++w) {
             uint32_t bits = words[w];
             while (bits) {

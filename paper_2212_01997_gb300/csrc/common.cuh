@@ -84,3 +84,26 @@ __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
 }
+
+// double -> float, round to nearest even, by integer operations (finite
+// values; magnitudes below the smallest normal float flush to zero).  Keeps
+// per-element work off GB300's narrow FP64 pipe.
+__device__ __forceinline__ float d2f_rn(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const uint32_t sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    if (e <= 0) return __uint_as_float(sign);
+    if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+    const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);  // top 23 of 52 mantissa bits
+    const uint32_t rem = lo & 0x1fffffffu;                    // the 29 dropped bits
+    uint32_t f = ((uint32_t)e << 23) + m;                     // a carry moves into the exponent
+    if (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) f += 1u;
+    return __uint_as_float(sign | f);
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+

@@ -67,40 +67,89 @@ __global__ void k_check_finite(int64_t nnz, const double* v, int* err) {
         if (!isfinite(v[e])) set_error(err, GB_ERR_NAN);
 }
 
-__global__ void k_gershgorin(int32_t n_sub, const int64_t* sub_ptr, const int32_t* sub_idx,
-                             const int64_t* Hptr, const int32_t* Hidx, const double* Hval,
-                             double* eps_lo, double* eps_hi) {
-    __shared__ double slo[FP64_THREADS], shi[FP64_THREADS];
+// Gershgorin interval of every h^(i) = H[S_i, S_i]: the lanes of a warp walk
+// one row's non-zeros, the subgraph's vertex list in shared memory when it
+// fits.  The radius is summed in FP32 (values converted by integer
+// operations) and widened by 2^-16, which covers the conversions and the
+// rounding of up to 2^15 terms: the interval stays an enclosure.  Diagonal
+// and interval ends stay FP64, but the FP64 work is done once per 32 rows
+// (lane k finishes row k of its warp's batch): GB300's FP64 pipe is narrow.
+constexpr int GERSH_THREADS = 128;
+constexpr int GERSH_SMEM_N = 2048;
+__global__ void __launch_bounds__(GERSH_THREADS) k_gershgorin(int32_t n_sub, const int64_t* sub_ptr,
+                                                              const int32_t* sub_idx, const int64_t* Hptr,
+                                                              const int32_t* Hidx, const double* Hval,
+                                                              double* eps_lo, double* eps_hi) {
+    __shared__ int32_t Ss[GERSH_SMEM_N];
+    __shared__ double wlo[GERSH_THREADS / 32], whi[GERSH_THREADS / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = GERSH_THREADS / 32;
     for (int32_t i = blockIdx.x; i < n_sub; i += gridDim.x) {
-        const int32_t* S = sub_idx + sub_ptr[i];
         const int n = (int)(sub_ptr[i + 1] - sub_ptr[i]);
+        const int32_t* S = sub_idx + sub_ptr[i];
+        if (n <= GERSH_SMEM_N) {
+            for (int r = threadIdx.x; r < n; r += GERSH_THREADS) Ss[r] = S[r];
+            S = Ss;
+        }
+        __syncthreads();
         double lo = INFINITY, hi = -INFINITY;
-        for (int r = threadIdx.x; r < n; r += blockDim.x) {
-            const int32_t g = S[r];
-            double diag = 0.0, rad = 0.0;
-            for (int64_t p = Hptr[g]; p < Hptr[g + 1]; ++p) {
-                int32_t c = Hidx[p];
-                int lc = lower_bound_i32(S, n, c);
-                if (lc < n && S[lc] == c) {
-                    if (lc == r) diag = Hval[p]; else rad += fabs(Hval[p]);
+        for (int rb = warp * 32; rb < n; rb += nw * 32) {
+            float my_rad = 0.f;
+            uint32_t my_dhi = 0u, my_dlo = 0u;  // bits of row (rb + lane)'s diagonal
+            const int kn = min(32, n - rb);
+            for (int k = 0; k < kn; ++k) {
+                const int r = rb + k;
+                const int32_t g = S[r];
+                float rad = 0.f;
+                bool has = false;
+                uint32_t dhi = 0u, dlo = 0u;
+                for (int64_t p = Hptr[g] + lane; p < Hptr[g + 1]; p += 32) {
+                    const int32_t c = Hidx[p];
+                    const int lc = lower_bound_i32(S, n, c);
+                    if (lc < n && S[lc] == c) {
+                        if (lc == r) {
+                            const unsigned long long b = (unsigned long long)__double_as_longlong(Hval[p]);
+                            dhi = (uint32_t)(b >> 32);
+                            dlo = (uint32_t)b;
+                            has = true;
+                        } else {
+                            rad += fabsf(d2f_rn(Hval[p]));
+                        }
+                    }
+                }
+                for (int o = 16; o > 0; o >>= 1) rad += __shfl_xor_sync(0xffffffffu, rad, o);
+                const uint32_t bal = __ballot_sync(0xffffffffu, has);
+                const int src = bal ? __ffs(bal) - 1 : 0;
+                dhi = __shfl_sync(0xffffffffu, dhi, src);
+                dlo = __shfl_sync(0xffffffffu, dlo, src);
+                if (lane == k) {
+                    my_rad = rad;
+                    my_dhi = bal ? dhi : 0u;
+                    my_dlo = bal ? dlo : 0u;
                 }
             }
-            lo = fmin(lo, diag - rad);
-            hi = fmax(hi, diag + rad);
-        }
-        slo[threadIdx.x] = lo;
-        shi[threadIdx.x] = hi;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o) {
-                slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + o]);
-                shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + o]);
+            if (lane < kn) {
+                const double diag = __longlong_as_double((long long)(((unsigned long long)my_dhi << 32) | my_dlo));
+                const double rd = (double)my_rad * (1.0 + 0x1p-16);
+                lo = fmin(lo, diag - rd);
+                hi = fmax(hi, diag + rd);
             }
-            __syncthreads();
         }
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) {
+            wlo[warp] = lo;
+            whi[warp] = hi;
+        }
+        __syncthreads();
         if (threadIdx.x == 0) {
-            eps_lo[i] = slo[0];
-            eps_hi[i] = shi[0];
+            for (int w = 1; w < nw; ++w) {
+                lo = fmin(lo, wlo[w]);
+                hi = fmax(hi, whi[w]);
+            }
+            eps_lo[i] = lo;
+            eps_hi[i] = hi;
         }
         __syncthreads();
     }
@@ -498,7 +547,7 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
     GB_CUDA(cudaMemsetAsync(L.moff + n_sub, 0, sizeof(int64_t), st));
     GB_TRY(exclusive_scan_i64(h, L.moff, L.moff, (int64_t)n_sub + 1, L.scan_tmp));
     // spectral bounds
-    GB_LAUNCH(h, k_gershgorin, sub_grid, FP64_THREADS, 0, n_sub, P->sub_ptr, P->sub_idx, H->ptr, H->idx,
+    GB_LAUNCH(h, k_gershgorin, sub_grid, GERSH_THREADS, 0, n_sub, P->sub_ptr, P->sub_idx, H->ptr, H->idx,
               H->val, L.eps_lo, L.eps_hi);
     const int stride = TR_FIXED + m;
     GB_LAUNCH(h, k_reduce, 1, FP64_THREADS, 0, n_sub, stride, (const double*)L.tr, (const double*)L.eps_lo,

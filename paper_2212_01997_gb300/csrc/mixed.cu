@@ -1137,12 +1137,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
 // Dense principal submatrices beta h^(i) = beta H[S_i, S_i] and beta h1_r^(i)
 // (FP32 in column groups of four, zero padding to npad), the FP64 diagonal of
 // h^(i), one block per subgraph, one warp per row.  Also the
-// largest row sum of |h1_r^(i)| (h1max[i * m + r]), which fixes the
-// perturbation's normalisation in the recursion.
+// largest row sum of |h1_r^(i)| (h1max[i * m + r], an upper bound: FP32 sums
+// widened by 2^-16), which fixes the perturbation's normalisation in the
+// recursion.  Per element only integer and FP32 work: the value is converted
+// by d2f_rn and scaled by beta in FP32 (within 1.5 float ulps of beta x).
 __global__ void __launch_bounds__(256) k_gather_dense(PassArgs a, float* hblk, double* hdiag) {
     __shared__ int32_t S[NMAX];
-    __shared__ double wmax[8];
+    __shared__ float wmax[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float bf = d2f_rn(a.beta);
     for (int32_t i = blockIdx.x; i < a.n_sub; i += gridDim.x) {
         const int64_t s0 = a.sub_ptr[i];
         const int n = (int)(a.sub_ptr[i + 1] - s0);
@@ -1151,9 +1154,10 @@ __global__ void __launch_bounds__(256) k_gather_dense(PassArgs a, float* hblk, d
             S[r] = a.sub_idx[s0 + r];
             hdiag[s0 + r] = 0.0;
         }
+        // blocks start on 64-element boundaries: zero them 16 bytes at a time
         for (int b = 0; b <= a.m; ++b) {
-            float* blk = hblk + (int64_t)b * a.hblk_stride + a.boff[i];
-            for (int e = threadIdx.x; e < npad * npad; e += blockDim.x) blk[e] = 0.f;
+            float4* blk4 = (float4*)(hblk + (int64_t)b * a.hblk_stride + a.boff[i]);
+            for (int e = threadIdx.x; e < npad * npad / 4; e += blockDim.x) blk4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncthreads();
         for (int b = 0; b <= a.m; ++b) {
@@ -1161,10 +1165,10 @@ __global__ void __launch_bounds__(256) k_gather_dense(PassArgs a, float* hblk, d
             const int32_t* idx = b == 0 ? a.Hidx : a.H1idx[b - 1];
             const double* val = b == 0 ? a.Hval : a.H1val[b - 1];
             float* blk = hblk + (int64_t)b * a.hblk_stride + a.boff[i];
-            double rmax = 0.0;
+            float rmax = 0.f;
             for (int r = warp; r < n; r += blockDim.x / 32) {
                 const int32_t g = S[r];
-                double rs = 0.0;
+                float rs = 0.f;
                 for (int64_t p = ptr[g] + lane; p < ptr[g + 1]; p += 32) {
                     const int32_t col = idx[p];
                     int lo = 0, hi = n;
@@ -1174,20 +1178,22 @@ __global__ void __launch_bounds__(256) k_gather_dense(PassArgs a, float* hblk, d
                     }
                     if (lo < n && S[lo] == col) {
                         const double x = val[p];
-                        blk[((size_t)(lo >> 2) * npad + r) * 4 + (lo & 3)] = (float)(a.beta * x);
+                        const float v = bf * d2f_rn(x);
+                        blk[((size_t)(lo >> 2) * npad + r) * 4 + (lo & 3)] = v;
                         if (b == 0 && lo == r) hdiag[s0 + r] = x;
-                        rs += fabs(x);
+                        rs += fabsf(v);
                     }
                 }
-                rmax = fmax(rmax, warp_sum(rs));  // lane 0 holds the row sum
+                rmax = fmaxf(rmax, warp_sum_f(rs));  // lane 0 holds the row sum
             }
             if (b > 0) {
                 if (lane == 0) wmax[warp] = rmax;
                 __syncthreads();
                 if (threadIdx.x == 0) {
-                    double v = wmax[0];
-                    for (int w = 1; w < (int)(blockDim.x / 32); ++w) v = fmax(v, wmax[w]);
-                    a.h1max[(int64_t)i * a.m + (b - 1)] = v;
+                    float v = wmax[0];
+                    for (int w = 1; w < (int)(blockDim.x / 32); ++w) v = fmaxf(v, wmax[w]);
+                    // sum of |beta h1| in FP32 (<= 128 terms, each within 2^-23)
+                    a.h1max[(int64_t)i * a.m + (b - 1)] = (double)v * (1.0 + 0x1p-16) / a.beta;
                 }
                 __syncthreads();
             }
