@@ -156,32 +156,52 @@ __global__ void __launch_bounds__(GERSH_THREADS) k_gershgorin(int32_t n_sub, con
 }
 
 // Single-block reduction in a fixed order (deterministic): sums of the
-// per-subgraph trace slots, min of eps_lo and max of eps_hi.
-__global__ void k_reduce(int32_t n_sub, int32_t stride, const double* tr, const double* eps_lo,
-                         const double* eps_hi, double* sums, double* bounds) {
-    __shared__ double sh[FP64_THREADS];
-    for (int k = 0; k < stride + 2; ++k) {
-        // 0: sum, 1: min, 2: max
-        const int op = (k < stride) ? (k == TR_MAXW ? 2 : 0) : (k == stride ? 1 : 2);
-        double v = op == 0 ? 0.0 : (op == 1 ? INFINITY : -INFINITY);
-        for (int32_t i = threadIdx.x; i < n_sub; i += blockDim.x) {
-            const double x = k < stride ? tr[(int64_t)i * stride + k] : (k == stride ? eps_lo[i] : eps_hi[i]);
-            v = op == 0 ? v + x : (op == 1 ? fmin(v, x) : fmax(v, x));
+// per-subgraph trace slots, min of eps_lo and max of eps_hi.  Thread t owns a
+// fixed contiguous range of subgraphs and accumulates every quantity of it in
+// one sweep; the threads' partials are then combined by a fixed tree.
+constexpr int REDUCE_THREADS = 256;  // (stride + 2) x 256 doubles <= 30 KB of shared memory
+constexpr int REDUCE_MAXQ = TR_FIXED + GB_MAX_RHS + 2;
+__global__ void __launch_bounds__(REDUCE_THREADS) k_reduce(int32_t n_sub, int32_t stride, const double* tr,
+                                                           const double* eps_lo, const double* eps_hi,
+                                                           double* sums, double* bounds) {
+    extern __shared__ double sh[];  // [stride + 2][REDUCE_THREADS]
+    const int nq = stride + 2;
+    const int t = threadIdx.x;
+    const int32_t per = (n_sub + REDUCE_THREADS - 1) / REDUCE_THREADS;
+    const int32_t i0 = min(n_sub, t * per), i1 = min(n_sub, i0 + per);
+    double v[REDUCE_MAXQ];
+#pragma unroll
+    for (int k = 0; k < REDUCE_MAXQ; ++k) v[k] = 0.0;
+    v[TR_MAXW] = -INFINITY;
+    double lo = INFINITY, hi = -INFINITY;
+    for (int32_t i = i0; i < i1; ++i) {
+        const double* row = tr + (int64_t)i * stride;
+#pragma unroll
+        for (int k = 0; k < REDUCE_MAXQ - 2; ++k) {
+            if (k < stride) v[k] = k == TR_MAXW ? fmax(v[k], row[k]) : v[k] + row[k];
         }
-        sh[threadIdx.x] = v;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o) {
-                double a = sh[threadIdx.x], b = sh[threadIdx.x + o];
-                sh[threadIdx.x] = op == 0 ? a + b : (op == 1 ? fmin(a, b) : fmax(a, b));
+        lo = fmin(lo, eps_lo[i]);
+        hi = fmax(hi, eps_hi[i]);
+    }
+#pragma unroll
+    for (int k = 0; k < REDUCE_MAXQ - 2; ++k)
+        if (k < stride) sh[k * REDUCE_THREADS + t] = v[k];
+    sh[stride * REDUCE_THREADS + t] = lo;
+    sh[(stride + 1) * REDUCE_THREADS + t] = hi;
+    __syncthreads();
+    for (int o = REDUCE_THREADS / 2; o > 0; o >>= 1) {
+        if (t < o) {
+            for (int k = 0; k < nq; ++k) {
+                const double a = sh[k * REDUCE_THREADS + t], b = sh[k * REDUCE_THREADS + t + o];
+                const int op = k < stride ? (k == TR_MAXW ? 2 : 0) : (k == stride ? 1 : 2);  // sum, min, max
+                sh[k * REDUCE_THREADS + t] = op == 0 ? a + b : (op == 1 ? fmin(a, b) : fmax(a, b));
             }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            if (k < stride) sums[k] = sh[0];
-            else bounds[k - stride] = sh[0];
         }
         __syncthreads();
+    }
+    if (t < nq) {
+        if (t < stride) sums[t] = sh[t * REDUCE_THREADS];
+        else bounds[t - stride] = sh[t * REDUCE_THREADS];
     }
 }
 
@@ -546,18 +566,7 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
     GB_LAUNCH(h, k_block_sizes, (n_sub + tb - 1) / tb, tb, 0, n_sub, P->sub_ptr, L.moff, split ? 1 : 0);
     GB_CUDA(cudaMemsetAsync(L.moff + n_sub, 0, sizeof(int64_t), st));
     GB_TRY(exclusive_scan_i64(h, L.moff, L.moff, (int64_t)n_sub + 1, L.scan_tmp));
-    // spectral bounds
-    GB_LAUNCH(h, k_gershgorin, sub_grid, GERSH_THREADS, 0, n_sub, P->sub_ptr, P->sub_idx, H->ptr, H->idx,
-              H->val, L.eps_lo, L.eps_hi);
     const int stride = TR_FIXED + m;
-    GB_LAUNCH(h, k_reduce, 1, FP64_THREADS, 0, n_sub, stride, (const double*)L.tr, (const double*)L.eps_lo,
-              (const double*)L.eps_hi, L.sums, L.bounds);
-    double bounds[2];
-    GB_TRY(read_f64(h, L.bounds, bounds, 2));
-    int herr = 0;
-    GB_TRY(read_i32(h, L.err, &herr));
-    if (herr) return herr;
-
     PassArgs a;
     memset(&a, 0, sizeof(a));
     a.n_sub = n_sub;
@@ -598,9 +607,22 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
     a.hdiag = L.hdiag;
     a.h1max = L.h1max;
     a.err = L.err;
-    // split path: dense principal submatrices of H and H1 once per call (they
-    // do not depend on mu)
-    if (split) GB_TRY(launch_split_gather(h, a, L.hblk, L.hdiag));
+    // spectral bounds.  Split path: the gather of the dense principal
+    // submatrices of H and H1 (once per call: they do not depend on mu) also
+    // yields the Gershgorin intervals.
+    if (split) {
+        GB_TRY(launch_split_gather(h, a, L.hblk, L.hdiag));
+    } else {
+        GB_LAUNCH(h, k_gershgorin, sub_grid, GERSH_THREADS, 0, n_sub, P->sub_ptr, P->sub_idx, H->ptr, H->idx,
+                  H->val, L.eps_lo, L.eps_hi);
+    }
+    GB_LAUNCH(h, k_reduce, 1, REDUCE_THREADS, sizeof(double) * (stride + 2) * REDUCE_THREADS, n_sub, stride, (const double*)L.tr, (const double*)L.eps_lo,
+              (const double*)L.eps_hi, L.sums, L.bounds);
+    double bounds[2];
+    GB_TRY(read_f64(h, L.bounds, bounds, 2));
+    int herr = 0;
+    GB_TRY(read_i32(h, L.err, &herr));
+    if (herr) return herr;
 
     // mu: Newton-Raphson on the core traces (Eq. NewtonRaphson), safeguarded
     // by a bisection bracket; each evaluation is one full pass.
@@ -626,7 +648,7 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
             GB_LAUNCH(h, k_fermi_fp64, sub_grid, FP64_THREADS, 0, a);
         }
         GB_CUDA(cudaEventRecord(ev1, st));
-        GB_LAUNCH(h, k_reduce, 1, FP64_THREADS, 0, n_sub, stride, (const double*)L.tr,
+        GB_LAUNCH(h, k_reduce, 1, REDUCE_THREADS, sizeof(double) * (stride + 2) * REDUCE_THREADS, n_sub, stride, (const double*)L.tr,
                   (const double*)L.eps_lo, (const double*)L.eps_hi, L.sums, L.bounds);
         GB_TRY(read_f64(h, L.sums, sums, stride));
         {

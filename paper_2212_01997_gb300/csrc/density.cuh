@@ -47,8 +47,8 @@ struct PassArgs {
     int32_t min_steps;
     int32_t ns_iters;
     int32_t split_kind;  // 0: FP16 parts, 1: BF16 parts (split-precision kernel only)
-    const double* eps_lo;
-    const double* eps_hi;
+    double* eps_lo;  // per-subgraph Gershgorin interval (written by the split path's gather)
+    double* eps_hi;
     // outputs, at the positions of the collected CSC matrices
     const int64_t* col_ptr;
     double* Dval;

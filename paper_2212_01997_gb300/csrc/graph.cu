@@ -56,20 +56,30 @@ __global__ void k_edge_fill(int32_t n, const int64_t* ptr, const int32_t* idx, c
     }
 }
 
-// Row i: mark the (duplicated) edge list, then count or write it sorted.
+// Row i: mark the (duplicated) edge list, then count or write it sorted.  The
+// bitmap covers only the row's window [min, max] of neighbour indices (32-bit
+// aligned), so the clear and the compaction cost the window, not n.
 __global__ void k_row_unique(int32_t n, const int64_t* off, const int32_t* edges,
                              int64_t* count, const int64_t* out_ptr, int32_t* out_idx) {
     extern __shared__ uint32_t words[];
     __shared__ int64_t scan[ROW_THREADS];
-    const int W = (n + 31) >> 5;
+    __shared__ int32_t red[2 * (ROW_THREADS / 32)];
     for (int32_t i = blockIdx.x; i < n; i += gridDim.x) {
-        bitmap_clear(words, W);
+        int32_t jmin = INT32_MAX, jmax = -1;
+        for (int64_t e = off[i] + threadIdx.x; e < off[i + 1]; e += blockDim.x) {
+            const int32_t j = edges[e];
+            jmin = min(jmin, j);
+            jmax = max(jmax, j);
+        }
+        int32_t base;
+        int W;
+        bitmap_window(jmin, jmax, red, base, W);
+        bitmap_clear(words, W);  // (its barrier also retires the window's scratch reads)
         for (int64_t e = off[i] + threadIdx.x; e < off[i + 1]; e += blockDim.x)
-            bitmap_set(words, edges[e]);
+            bitmap_set(words, edges[e] - base);
         __syncthreads();
-        int64_t c = bitmap_compact(words, W, out_idx ? out_idx + out_ptr[i] : nullptr, scan);
+        int64_t c = bitmap_compact(words, W, out_idx ? out_idx + out_ptr[i] : nullptr, scan, base);
         if (threadIdx.x == 0 && count) count[i] = c;
-        __syncthreads();
     }
 }
 

@@ -1136,14 +1136,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
 
 // Dense principal submatrices beta h^(i) = beta H[S_i, S_i] and beta h1_r^(i)
 // (FP32 in column groups of four, zero padding to npad), the FP64 diagonal of
-// h^(i), one block per subgraph, one warp per row.  Also the
-// largest row sum of |h1_r^(i)| (h1max[i * m + r], an upper bound: FP32 sums
+// h^(i), one block per subgraph, one warp per row.  Also the Gershgorin
+// interval of h^(i) (eps_lo/eps_hi, FP32 sums widened to an enclosure; this
+// path needs no separate bounds kernel) and the largest row sum of |h1_r^(i)| (h1max[i * m + r], an upper bound: FP32 sums
 // widened by 2^-16), which fixes the perturbation's normalisation in the
 // recursion.  Per element only integer and FP32 work: the value is converted
 // by d2f_rn and scaled by beta in FP32 (within 1.5 float ulps of beta x).
 __global__ void __launch_bounds__(256) k_gather_dense(PassArgs a, float* hblk, double* hdiag) {
     __shared__ int32_t S[NMAX];
-    __shared__ float wmax[8];
+    __shared__ float wmax[8], wlo[8], whi[8], wab[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float bf = d2f_rn(a.beta);
     for (int32_t i = blockIdx.x; i < a.n_sub; i += gridDim.x) {
@@ -1166,9 +1167,10 @@ __global__ void __launch_bounds__(256) k_gather_dense(PassArgs a, float* hblk, d
             const double* val = b == 0 ? a.Hval : a.H1val[b - 1];
             float* blk = hblk + (int64_t)b * a.hblk_stride + a.boff[i];
             float rmax = 0.f;
+            float glo = INFINITY, ghi = -INFINITY, gab = 0.f;  // Gershgorin interval (b = 0)
             for (int r = warp; r < n; r += blockDim.x / 32) {
                 const int32_t g = S[r];
-                float rs = 0.f;
+                float rs = 0.f, rad = 0.f, dgf = 0.f;
                 for (int64_t p = ptr[g] + lane; p < ptr[g + 1]; p += 32) {
                     const int32_t col = idx[p];
                     int lo = 0, hi = n;
@@ -1178,13 +1180,51 @@ __global__ void __launch_bounds__(256) k_gather_dense(PassArgs a, float* hblk, d
                     }
                     if (lo < n && S[lo] == col) {
                         const double x = val[p];
-                        const float v = bf * d2f_rn(x);
+                        const float xf = d2f_rn(x), v = bf * xf;
                         blk[((size_t)(lo >> 2) * npad + r) * 4 + (lo & 3)] = v;
-                        if (b == 0 && lo == r) hdiag[s0 + r] = x;
+                        if (b == 0) {
+                            if (lo == r) {
+                                hdiag[s0 + r] = x;
+                                dgf = xf;
+                            } else {
+                                rad += fabsf(xf);
+                            }
+                        }
                         rs += fabsf(v);
                     }
                 }
                 rmax = fmaxf(rmax, warp_sum_f(rs));  // lane 0 holds the row sum
+                if (b == 0) {
+                    // Gershgorin row (every lane gets the sums)
+                    for (int o = 16; o > 0; o >>= 1) {
+                        rad += __shfl_xor_sync(0xffffffffu, rad, o);
+                        dgf += __shfl_xor_sync(0xffffffffu, dgf, o);  // one lane holds it
+                    }
+                    glo = fminf(glo, dgf - rad);
+                    ghi = fmaxf(ghi, dgf + rad);
+                    gab = fmaxf(gab, fabsf(dgf) + rad);
+                }
+            }
+            if (b == 0) {
+                if (lane == 0) {
+                    wlo[warp] = glo;
+                    whi[warp] = ghi;
+                    wab[warp] = gab;
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    for (int w = 1; w < (int)(blockDim.x / 32); ++w) {
+                        glo = fminf(glo, wlo[w]);
+                        ghi = fmaxf(ghi, whi[w]);
+                        gab = fmaxf(gab, wab[w]);
+                    }
+                    // FP32 terms within 2^-24 each, <= 127 of them per radius:
+                    // widening by 2^-16 of max(|h_rr| + radius) keeps an enclosure
+                    const double wd = (double)gab * 0x1p-16;
+                    a.eps_lo[i] = (double)glo - wd;
+                    a.eps_hi[i] = (double)ghi + wd;
+                }
+                __syncthreads();
             }
             if (b > 0) {
                 if (lane == 0) wmax[warp] = rmax;

@@ -58,22 +58,40 @@ __global__ void k_subgraphs(int32_t n, int32_t n_sub, const int64_t* gptr, const
                             int* stats) {
     extern __shared__ uint32_t words[];
     __shared__ int64_t scan[SUB_THREADS];
-    const int W = (n + 31) >> 5;
+    __shared__ int32_t red[2 * (SUB_THREADS / 32)];
     for (int32_t i = blockIdx.x; i < n_sub; i += gridDim.x) {
         const int64_t c0 = core_ptr[i], c1 = core_ptr[i + 1];
+        // the window of the core and its neighbours (bitmaps cost the window, not n)
+        int32_t lo = INT32_MAX, hi = -1;
+        for (int64_t e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
+            const int32_t v = core_idx[e];
+            lo = min(lo, v);
+            hi = max(hi, v);
+        }
+        for (int64_t e = c0; e < c1; ++e) {
+            const int32_t v = core_idx[e];
+            for (int64_t f = gptr[v] + threadIdx.x; f < gptr[v + 1]; f += blockDim.x) {
+                const int32_t u = gidx[f];
+                lo = min(lo, u);
+                hi = max(hi, u);
+            }
+        }
+        int32_t base;
+        int W;
+        bitmap_window(lo, hi, red, base, W);
         if (mode == 0) {
             // sorted core (the atomic fill leaves an arbitrary order)
             bitmap_clear(words, W);
-            for (int64_t e = c0 + threadIdx.x; e < c1; e += blockDim.x) bitmap_set(words, core_idx[e]);
+            for (int64_t e = c0 + threadIdx.x; e < c1; e += blockDim.x) bitmap_set(words, core_idx[e] - base);
             __syncthreads();
-            bitmap_compact(words, W, core_idx + c0, scan);
+            bitmap_compact(words, W, core_idx + c0, scan, base);
         }
         bitmap_clear(words, W);
         for (int64_t e = c0; e < c1; ++e) {
             int32_t v = core_idx[e];
-            if (threadIdx.x == 0) bitmap_set(words, v);
+            if (threadIdx.x == 0) bitmap_set(words, v - base);
             for (int64_t f = gptr[v] + threadIdx.x; f < gptr[v + 1]; f += blockDim.x)
-                bitmap_set(words, gidx[f]);
+                bitmap_set(words, gidx[f] - base);
         }
         __syncthreads();
         if (mode == 0) {
@@ -85,7 +103,7 @@ __global__ void k_subgraphs(int32_t n, int32_t n_sub, const int64_t* gptr, const
             }
         } else {
             int32_t* out = sub_idx + sub_ptr[i];
-            int64_t s = bitmap_compact(words, W, out, scan);
+            int64_t s = bitmap_compact(words, W, out, scan, base);
             __syncthreads();
             for (int64_t e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
                 int32_t v = core_idx[e];
