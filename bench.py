@@ -98,6 +98,8 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=2)
     p.add_argument("--companion", default="water10k_kT0.05")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--split-small", type=int, default=-1,
+                   help="npad bound of the small split configuration (-1: autotuned per workload)")
     p.add_argument("--trajectory", action="store_true",
                    help="the rank-m workload instead: m=6 responses along a thermal trajectory of "
                         "20,000 waters (steps/s, p50/p99 step latency)")
@@ -202,6 +204,10 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
+# npad bound of the small split configuration (set in main)
+SPLIT_SMALL = {"npad": 0, "auto": False}
+
+
 def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world, dist, e2e_steps=0):
     """Time the whole hot path on one workload; return the measurements."""
     import numpy as np
@@ -226,7 +232,8 @@ def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world,
                          handle=handle)
         launches["n"] += handle.lib.gb_launch_count(handle.h)
         R = gb.density_and_response(Hs, H1s, wl.kT, system.n_electrons, P, precision=precision, mu0=mu0,
-                                    handle=handle, max_newton=max_newton, raise_on_error=max_newton == 0)
+                                    handle=handle, max_newton=max_newton, raise_on_error=max_newton == 0,
+                                    split_small_npad=SPLIT_SMALL["npad"] if precision != "fp64" else 0)
         launches["n"] += R.report["kernel_launches"]
         return P, R
 
@@ -266,6 +273,16 @@ def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world,
     _, R1, _, _, _, _, _, _ = timed("fp16x3", 0, 1, math.nan, None)
     d_1 = R1.D
     _, R0, _, _, _, _, _, _ = timed("fp16x3", 0, max(warmup, 3), R1.mu, d_1)
+    if SPLIT_SMALL["auto"]:
+        # size bins -> configuration (gb_plan_autotune), outside the timed region
+        Gp = gb.graph_build(H, wl.tau, d_prev=d_1, handle=handle)
+        Pp = gb.partition(Gp, groups, n_groups, subgroups=atoms, n_subgroups=n_atoms, max_sub=SUB_CAP,
+                          handle=handle)
+        plan = gb.plan_autotune(H, H1, wl.kT, system.n_electrons, Pp, R0.mu, handle=handle)
+        SPLIT_SMALL["npad"] = plan["split_small_npad"]
+        out["split_plan"] = plan
+        _, R0, _, _, _, _, _, _ = timed("fp16x3", 0, 1, R0.mu, d_1)
+    out["split_small_npad"] = SPLIT_SMALL["npad"]
     clocks = ClockSampler(dev.index or 0)
     clocks.start()
     P, Rm, t_m, k_m, pass_m, fl_m, n_launch, dp = timed("fp16x3", steps, 0, R0.mu, d_1)
@@ -454,6 +471,8 @@ def run_trajectory(args, rank, world):
 
 def main():
     args = parse()
+    SPLIT_SMALL["npad"] = max(args.split_small, 0)
+    SPLIT_SMALL["auto"] = args.split_small < 0
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
@@ -514,6 +533,7 @@ def main():
                        "n_orbitals": system.n_orb, "n_subgraphs": head["P"].n_sub,
                        "max_subgraph": head["P"].max_sub, "mean_subgraph": round(head["mean_sub"], 1),
                        "m": 1, "kT": wl.kT, "tau": wl.tau,
+                       "split_small_npad": head["split_small_npad"], "split_plan": head.get("split_plan"),
                        "l2": "flushed (512 MB write) before every timed step",
                        "parallelism": f"replicas x{world} (independent systems, no collective)",
                        "step": ("graph_build(H, D_1) + capped partition + density_and_response "

@@ -121,6 +121,11 @@ typedef struct gb_opts {
                             When a Newton step no longer halves the residual (trace
                             round-off floor) mu is accepted once that bound is within
                             100 tol_d (split precision) or 10 tol_d (FP64).                 */
+    int32_t split_small_npad; /* split precision: subgraphs with round16(|S_i|) <= this (0, 16,
+                            32, 48 or 64) run in the small configuration, two CTAs per SM,
+                            the rest in the 128-column one.  0: all in the 128-column one.
+                            gb_plan_autotune picks it.  Results do not depend on it beyond
+                            summation order in the core-column refinement.                 */
 } gb_opts;
 
 typedef struct gb_report {
@@ -291,6 +296,38 @@ int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_csr* H1, int
                             double kT, double n_electrons, const gb_part* P,
                             const gb_opts* opts, double* mu_inout, gb_csc* D, gb_csc* D1,
                             double* mu1, gb_report* rep);
+
+/* ---- gb_plan_autotune ----------------------------------------------------- *
+ * Size bins -> kernel configuration for the split-precision recursion.  The
+ * subgraphs are binned by npad = round16(|S_i|) (16, 32, ..., 128); those in
+ * bins <= split_small_npad run in the small configuration (8 warps, 256 TMEM
+ * columns, two CTAs per SM, so one CTA's staging overlaps the other's MMAs),
+ * the rest in the 128-column one (12 warps, one CTA per SM).  Candidates are
+ * 0 and every bin edge 16..64 that moves at least one subgraph; each is timed
+ * as the device time of one recursion pass (CUDA events) at the fixed mu, the
+ * second of two passes, with the caller's inputs and output buffers (which
+ * hold that pass on return).  The choice is the fastest candidate, the
+ * smallest threshold among those within 2% of it: a function of the timing
+ * table alone.  The handle caches the last plan by (n_sub, total size, m,
+ * precision); a repeated call with the same key returns it without timing.
+ *   H, H1, m, kT, n_electrons, P, D, D1: as gb_density_and_response.
+ *   opts     [host] options of the calls the plan is for (split precision);
+ *            split_small_npad and max_newton are overridden while timing.
+ *   mu       fixed chemical potential of the timed passes (eV).
+ *   plan     out, [host].
+ * Errors: those of gb_density_and_response; GB_ERR_ARG for an FP64 opts. */
+#define GB_PLAN_MAX_CAND 5
+typedef struct gb_plan {
+    int32_t split_small_npad;              /* the choice: pass as gb_opts.split_small_npad  */
+    int32_t n_candidates;
+    int32_t candidate[GB_PLAN_MAX_CAND];   /* thresholds timed, ascending                  */
+    double pass_ms[GB_PLAN_MAX_CAND];      /* recursion device time of one pass            */
+    int64_t bin_count[8];                  /* subgraphs with npad = 16 (k + 1)              */
+    int32_t cached;                        /* 1: returned from the handle's cache          */
+} gb_plan;
+int gb_plan_autotune(gb_handle* h, const gb_csr* H, const gb_csr* H1, int32_t m, double kT,
+                     double n_electrons, const gb_part* P, const gb_opts* opts, double mu,
+                     gb_csc* D, gb_csc* D1, gb_plan* plan);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,7 @@ from . import _lib as L
 from ._lib import GbError, PRECISION
 
 __all__ = ["DeviceCSR", "Graph", "Partition", "CSC", "Result", "Handle", "graph_build", "partition",
-           "density_and_response", "GbError", "PRECISION", "library"]
+           "density_and_response", "plan_autotune", "GbError", "PRECISION", "library"]
 
 
 def library():
@@ -234,7 +234,7 @@ def partition(G: Graph, groups: torch.Tensor | None = None, n_groups: int | None
 def density_and_response(H: DeviceCSR, H1: list, kT: float, n_electrons: float, part: Partition, *,
                          precision: str = "fp64", mu0: float = math.nan, max_newton: int = 0,
                          tol_occ: float = 0.0, min_steps: int = 0, ns_iters: int = 0, tol_d: float = 0.0,
-                         out: tuple | None = None, handle: Handle | None = None,
+                         split_small_npad: int = 0, out: tuple | None = None, handle: Handle | None = None,
                          raise_on_error: bool = True) -> Result:
     """gb_density_and_response: D, D1, mu, mu1 on the partitioned graph.
 
@@ -244,7 +244,7 @@ def density_and_response(H: DeviceCSR, H1: list, kT: float, n_electrons: float, 
     lib = hd.lib
     m = len(H1)
     opts = L.gb_opts(PRECISION[precision], int(max_newton), float(tol_occ), int(min_steps), int(ns_iters),
-                     float(tol_d))
+                     float(tol_d), int(split_small_npad))
     ps = part.struct()
     nbytes = C.c_size_t()
     L.check("gb_density_workspace_size", lib.gb_density_workspace_size(C.byref(ps), m, C.byref(opts),
@@ -273,3 +273,45 @@ def density_and_response(H: DeviceCSR, H1: list, kT: float, n_electrons: float, 
         L.check("gb_density_and_response", st)
     report = {k: getattr(rep, k) for k, _ in L.gb_report._fields_}
     return Result(mu.value, [mu1[r] for r in range(m)], D, D1, st, report)
+
+
+def plan_autotune(H: DeviceCSR, H1: list, kT: float, n_electrons: float, part: Partition, mu: float, *,
+                  precision: str = "fp16x3", min_steps: int = 0, ns_iters: int = 0,
+                  out: tuple | None = None, handle: Handle | None = None) -> dict:
+    """gb_plan_autotune: the split configuration's size threshold for this partition.
+
+    Times one recursion pass per candidate (at the fixed ``mu``) and returns
+    the plan as a dict; pass ``plan["split_small_npad"]`` to
+    density_and_response.  The handle caches the plan by the partition's size.
+    """
+    if precision == "fp64":
+        raise ValueError("plan_autotune: the plan is for the split-precision recursion")
+    hd = handle or _default_handle(H.ptr.device)
+    lib = hd.lib
+    m = len(H1)
+    opts = L.gb_opts(PRECISION[precision], 1, 0.0, int(min_steps), int(ns_iters), 0.0, 0)
+    ps = part.struct()
+    nbytes = C.c_size_t()
+    L.check("gb_density_workspace_size", lib.gb_density_workspace_size(C.byref(ps), m, C.byref(opts),
+                                                                         C.byref(nbytes)))
+    hd.workspace(nbytes.value)
+    dev = hd.device
+    if out is None:
+        D = CSC(part.n, torch.empty(part.n + 1, dtype=torch.int64, device=dev),
+                torch.empty(part.out_nnz, dtype=torch.int32, device=dev),
+                torch.empty(part.out_nnz, dtype=torch.float64, device=dev))
+        D1 = [CSC(part.n, D.ptr, D.idx, torch.empty(part.out_nnz, dtype=torch.float64, device=dev))
+              for _ in range(m)]
+    else:
+        D, D1 = out
+    hs = H.struct()
+    h1s = (L.gb_csr * max(m, 1))(*[h.struct() for h in H1])
+    ds = D.struct()
+    d1s = (L.gb_csc * max(m, 1))(*[d.struct(with_index=False) for d in D1])
+    plan = L.gb_plan()
+    L.check("gb_plan_autotune", lib.gb_plan_autotune(hd.h, C.byref(hs), h1s, m, float(kT), float(n_electrons),
+                                                       C.byref(ps), C.byref(opts), float(mu), C.byref(ds), d1s,
+                                                       C.byref(plan)))
+    k = plan.n_candidates
+    return {"split_small_npad": plan.split_small_npad, "candidates": list(plan.candidate[:k]),
+            "pass_ms": list(plan.pass_ms[:k]), "bin_count": list(plan.bin_count), "cached": bool(plan.cached)}

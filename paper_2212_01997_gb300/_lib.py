@@ -47,7 +47,8 @@ class gb_part(C.Structure):
 
 class gb_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_newton", C.c_int32), ("tol_occ", C.c_double),
-                ("min_steps", C.c_int32), ("ns_iters", C.c_int32), ("tol_d", C.c_double)]
+                ("min_steps", C.c_int32), ("ns_iters", C.c_int32), ("tol_d", C.c_double),
+                ("split_small_npad", C.c_int32)]
 
 
 class gb_report(C.Structure):
@@ -57,6 +58,11 @@ class gb_report(C.Structure):
                 ("eps_min", C.c_double), ("eps_max", C.c_double), ("gemm_flops", C.c_double),
                 ("pass_kernel_ms", C.c_double), ("mu_d_bound", C.c_double),
                 ("kernel_launches", C.c_int64)]
+
+
+class gb_plan(C.Structure):
+    _fields_ = [("split_small_npad", C.c_int32), ("n_candidates", C.c_int32), ("candidate", C.c_int32 * 5),
+                ("pass_ms", C.c_double * 5), ("bin_count", C.c_int64 * 8), ("cached", C.c_int32)]
 
 
 # every entry point declared in include/gbqr.h: (name, restype, argtypes)
@@ -86,6 +92,9 @@ SIGNATURES = [
                                           C.c_double, C.c_double, C.POINTER(gb_part), C.POINTER(gb_opts),
                                           C.POINTER(C.c_double), C.POINTER(gb_csc), C.POINTER(gb_csc),
                                           C.POINTER(C.c_double), C.POINTER(gb_report)]),
+    ("gb_plan_autotune", C.c_int, [C.c_void_p, C.POINTER(gb_csr), C.POINTER(gb_csr), C.c_int32, C.c_double,
+                                   C.c_double, C.POINTER(gb_part), C.POINTER(gb_opts), C.c_double,
+                                   C.POINTER(gb_csc), C.POINTER(gb_csc), C.POINTER(gb_plan)]),
 ]
 
 _lib = None

@@ -19,7 +19,12 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libgbqr.so")
-SOURCES = ["api.cu", "graph.cu", "partition.cu", "density.cu", "mixed.cu"]
+# (source, object, defines): mixed.cu is compiled twice, once per size class of
+# the split-precision kernel
+SOURCES = [("api.cu", "api", []), ("graph.cu", "graph", []), ("partition.cu", "partition", []),
+           ("density.cu", "density", []), ("mixed.cu", "mixed", []),
+           ("mixed.cu", "mixed_listed", ["-DGB_SPLIT_LIST=1"]),
+           ("mixed.cu", "mixed_small", ["-DGB_SPLIT_NPMAX=64", "-DGB_SPLIT_LIST=1"])]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -30,10 +35,11 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the gbqr CUDA library cannot be built")
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+def _compile(unit: tuple, extra: list[str]) -> str:
+    src, name, defines = unit
+    obj = os.path.join(BUILD, name + ".o")
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-           "-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", obj, *extra]
+           "-I", INCLUDE, "-I", CSRC, *defines, "-c", os.path.join(CSRC, src), "-o", obj, *extra]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{res.stdout}\n{res.stderr}")

@@ -16,6 +16,7 @@ extern "C" int gb_create(gb_handle** h, void* stream) {
     p->required_ws = 0;
     p->launches = 0;
     p->ev0 = p->ev1 = nullptr;
+    p->plan_valid = 0;
     if (cudaGetDevice(&p->device) != cudaSuccess) {
         delete p;
         return GB_ERR_DEVICE;

@@ -18,6 +18,9 @@ struct gb_handle {
     int device;
     int64_t launches;  // kernels launched by the current call
     cudaEvent_t ev0, ev1;  // recursion-kernel timing (created on first use)
+    int plan_valid;        // gb_plan_autotune's cache: key (n_sub, sub_nnz, m, precision)
+    int64_t plan_key[4];
+    gb_plan plan;
 };
 
 #define GB_CUDA(call)                                   \

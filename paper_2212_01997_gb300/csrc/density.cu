@@ -205,6 +205,52 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_reduce(int32_t n_sub, int32_
     }
 }
 
+// The subgraphs of the two size classes of the split launches, each list in
+// ascending order: work[0, n0) with round16(|S_i|) > small, work[n_sub,
+// n_sub + n1) with round16(|S_i|) <= small; work_n = {n0, n1}.  One block;
+// thread t takes a fixed contiguous range, offsets by a block scan.
+constexpr int CLASS_THREADS = 1024;
+__global__ void __launch_bounds__(CLASS_THREADS) k_class_lists(int32_t n_sub, const int64_t* sub_ptr,
+                                                               int32_t small, int32_t* work, int32_t* work_n) {
+    __shared__ int32_t wsum[2][CLASS_THREADS / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int32_t per = (n_sub + CLASS_THREADS - 1) / CLASS_THREADS;
+    const int32_t i0 = min(n_sub, t * per), i1 = min(n_sub, i0 + per);
+    int32_t c1 = 0;
+    for (int32_t i = i0; i < i1; ++i) c1 += (int32_t)(((sub_ptr[i + 1] - sub_ptr[i] + 15) & ~15) <= small);
+    const int32_t c0 = (i1 - i0) - c1;
+    int32_t s0 = c0, s1 = c1;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y0 = __shfl_up_sync(0xffffffffu, s0, o), y1 = __shfl_up_sync(0xffffffffu, s1, o);
+        if (lane >= o) {
+            s0 += y0;
+            s1 += y1;
+        }
+    }
+    if (lane == 31) {
+        wsum[0][warp] = s0;
+        wsum[1][warp] = s1;
+    }
+    __syncthreads();
+    int32_t b0 = 0, b1 = 0, t0 = 0, t1 = 0;
+    for (int w = 0; w < CLASS_THREADS / 32; ++w) {
+        const int32_t v0 = wsum[0][w], v1 = wsum[1][w];
+        b0 += w < warp ? v0 : 0;
+        b1 += w < warp ? v1 : 0;
+        t0 += v0;
+        t1 += v1;
+    }
+    int32_t p0 = b0 + s0 - c0, p1 = b1 + s1 - c1;
+    for (int32_t i = i0; i < i1; ++i) {
+        if (((sub_ptr[i + 1] - sub_ptr[i] + 15) & ~15) <= small) work[n_sub + p1++] = i;
+        else work[p0++] = i;
+    }
+    if (t == 0) {
+        work_n[0] = t0;
+        work_n[1] = t1;
+    }
+}
+
 __global__ void k_d1_fixup(int64_t nnz, double mu1, const double* d1mu, double* d1) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
          e += (int64_t)gridDim.x * blockDim.x)
@@ -437,6 +483,8 @@ struct DensityLayout {
     float* hblk;        // split: (1 + m) * pool_stride dense gathered blocks (FP32)
     double* hdiag;      // split: sub_nnz FP64 diagonals of h^(i)
     double* h1max;      // split: n_sub * m largest |h1| row sums
+    int32_t* work;      // split: subgraph lists of the two size classes (2 x n_sub)
+    int32_t* work_n;    // split: their lengths (2)
     int64_t pool_stride;
 };
 
@@ -458,6 +506,8 @@ DensityLayout layout_density(Arena& ar, const gb_part* P, int32_t m, int precisi
         L.pool_stride = ((int64_t)P->max_sub * P->sub_nnz + 32 + 63) & ~(int64_t)63;
         L.pool = ar.take<double>((NBUF + m) * L.pool_stride);
         L.z1pool = nullptr;
+        L.work = nullptr;
+        L.work_n = nullptr;
         L.hblk = nullptr;
         L.hdiag = nullptr;
         L.h1max = nullptr;
@@ -472,6 +522,8 @@ DensityLayout layout_density(Arena& ar, const gb_part* P, int32_t m, int precisi
         L.hblk = ar.take<float>((1 + m) * L.pool_stride);
         L.hdiag = ar.take<double>(P->sub_nnz);
         L.h1max = ar.take<double>(n_sub * (int64_t)(m > 0 ? m : 1));
+        L.work = ar.take<int32_t>(2 * n_sub);
+        L.work_n = ar.take<int32_t>(8);
     }
     return L;
 }
@@ -516,9 +568,10 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
             return D1[r].val ? GB_ERR_CAPACITY : GB_ERR_ARG;
         }
     }
-    gb_opts o = {GB_PREC_FP64, 40, 0.0, 6, 0, 0.0};
+    gb_opts o = {GB_PREC_FP64, 40, 0.0, 6, 0, 0.0, 0};
     if (opts) o = *opts;
     if (o.precision < GB_PREC_FP64 || o.precision > GB_PREC_BF16X3) return GB_ERR_ARG;
+    if (o.split_small_npad < 0 || o.split_small_npad > 64 || o.split_small_npad % 16 != 0) return GB_ERR_ARG;
     const bool split = o.precision != GB_PREC_FP64;
     if (o.max_newton <= 0) o.max_newton = 40;
     if (o.min_steps <= 0) o.min_steps = 6;
@@ -611,6 +664,9 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
     // submatrices of H and H1 (once per call: they do not depend on mu) also
     // yields the Gershgorin intervals.
     if (split) {
+        if (o.split_small_npad > 0)
+            GB_LAUNCH(h, k_class_lists, 1, CLASS_THREADS, 0, n_sub, P->sub_ptr, o.split_small_npad, L.work,
+                      L.work_n);
         GB_TRY(launch_split_gather(h, a, L.hblk, L.hdiag));
     } else {
         GB_LAUNCH(h, k_gershgorin, sub_grid, GERSH_THREADS, 0, n_sub, P->sub_ptr, P->sub_idx, H->ptr, H->idx,
@@ -643,7 +699,18 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
         a.mu = mu;
         GB_CUDA(cudaEventRecord(ev0, st));
         if (split) {
-            GB_TRY(launch_split_pass(h, a));
+            // the 128-column configuration (for its size class when the small
+            // one takes subgraphs), then the small one
+            a.work = L.work;
+            a.work_n = L.work_n;
+            if (o.split_small_npad > 0) GB_TRY(launch_split_pass_listed(h, a));
+            else GB_TRY(launch_split_pass(h, a));
+            if (o.split_small_npad > 0) {
+                PassArgs b = a;
+                b.work = L.work + n_sub;
+                b.work_n = L.work_n + 1;
+                GB_TRY(launch_split_pass_small(h, b));
+            }
         } else {
             GB_LAUNCH(h, k_fermi_fp64, sub_grid, FP64_THREADS, 0, a);
         }
@@ -724,4 +791,74 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
         rep->kernel_launches = h->launches;
     }
     return converged ? GB_OK : GB_ERR_NO_CONVERGE;
+}
+
+// Size bins -> configuration: time one recursion pass per candidate threshold
+// (the second of two, at fixed mu) and keep the fastest; see gbqr.h.
+extern "C" int gb_plan_autotune(gb_handle* h, const gb_csr* H, const gb_csr* H1, int32_t m, double kT,
+                                double n_electrons, const gb_part* P, const gb_opts* opts, double mu,
+                                gb_csc* D, gb_csc* D1, gb_plan* plan) {
+    if (!h || !P || !opts || !plan || m < 0 || m > GB_MAX_RHS || !(mu == mu)) return GB_ERR_ARG;
+    if (opts->precision == GB_PREC_FP64 || P->n_sub <= 0 || !P->sub_ptr) return GB_ERR_ARG;
+    const int64_t key[4] = {P->n_sub, P->sub_nnz, m, opts->precision};
+    if (h->plan_valid && key[0] == h->plan_key[0] && key[1] == h->plan_key[1] && key[2] == h->plan_key[2] &&
+        key[3] == h->plan_key[3]) {
+        *plan = h->plan;
+        plan->cached = 1;
+        return GB_OK;
+    }
+    gb_plan pl;
+    memset(&pl, 0, sizeof(pl));
+    {
+        const int64_t n_sub = P->n_sub;
+        int64_t* sp = new (std::nothrow) int64_t[n_sub + 1];
+        if (!sp) return GB_ERR_ARG;
+        if (cudaMemcpyAsync(sp, P->sub_ptr, sizeof(int64_t) * (n_sub + 1), cudaMemcpyDeviceToHost, h->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            delete[] sp;
+            return GB_ERR_DEVICE;
+        }
+        for (int64_t i = 0; i < n_sub; ++i) {
+            const int64_t np = (sp[i + 1] - sp[i] + 15) / 16;  // bins of 16
+            if (np >= 1 && np <= 8) ++pl.bin_count[np - 1];
+        }
+        delete[] sp;
+    }
+    // candidates: 0 and each bin edge up to 64 that moves more subgraphs
+    pl.candidate[pl.n_candidates++] = 0;
+    int64_t moved = 0, prev = 0;
+    for (int t = 1; t <= 4; ++t) {
+        moved += pl.bin_count[t - 1];
+        if (moved > prev) pl.candidate[pl.n_candidates++] = 16 * t;
+        prev = moved;
+    }
+    double mu1[GB_MAX_RHS + 1];
+    for (int k = 0; k < pl.n_candidates; ++k) {
+        gb_opts o = *opts;
+        o.split_small_npad = pl.candidate[k];
+        o.max_newton = 1;
+        for (int rep = 0; rep < 2; ++rep) {
+            double mu_c = mu;
+            gb_report r;
+            memset(&r, 0, sizeof(r));
+            const int st = gb_density_and_response(h, H, H1, m, kT, n_electrons, P, &o, &mu_c, D, D1, mu1, &r);
+            if (st != GB_OK && st != GB_ERR_NO_CONVERGE) return st;
+            pl.pass_ms[k] = r.pass_kernel_ms;
+        }
+    }
+    double best = pl.pass_ms[0];
+    for (int k = 1; k < pl.n_candidates; ++k) best = pl.pass_ms[k] < best ? pl.pass_ms[k] : best;
+    for (int k = 0; k < pl.n_candidates; ++k) {
+        if (pl.pass_ms[k] <= 1.02 * best) {
+            pl.split_small_npad = pl.candidate[k];
+            break;
+        }
+    }
+    pl.cached = 0;
+    h->plan = pl;
+    for (int k = 0; k < 4; ++k) h->plan_key[k] = key[k];
+    h->plan_valid = 1;
+    *plan = pl;
+    return GB_OK;
 }

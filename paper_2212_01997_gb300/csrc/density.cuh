@@ -47,6 +47,8 @@ struct PassArgs {
     int32_t min_steps;
     int32_t ns_iters;
     int32_t split_kind;  // 0: FP16 parts, 1: BF16 parts (split-precision kernel only)
+    const int32_t* work;    // split launches: the subgraphs of this launch's size class,
+    const int32_t* work_n;  // ascending, and their count (device; see k_class_lists)
     double* eps_lo;  // per-subgraph Gershgorin interval (written by the split path's gather)
     double* eps_hi;
     // outputs, at the positions of the collected CSC matrices
@@ -89,4 +91,8 @@ __device__ __forceinline__ int recursion_steps(double beta, double mu, double lo
 }
 
 int launch_split_pass(gb_handle* h, const PassArgs& a);
+// the same recursion over a list of subgraphs (a.work): the 128-column
+// configuration, and the small one for round16(|S_i|) <= 64 (two CTAs per SM)
+int launch_split_pass_listed(gb_handle* h, const PassArgs& a);
+int launch_split_pass_small(gb_handle* h, const PassArgs& a);
 int launch_split_gather(gb_handle* h, const PassArgs& a, float* hblk, double* hdiag);

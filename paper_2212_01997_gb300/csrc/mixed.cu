@@ -49,17 +49,52 @@
 
 namespace {
 
-constexpr int THREADS = 384;  // 12 warps: 4 TMEM lane quadrants x 3 column groups
+// The file is compiled twice: the default configuration (GB_SPLIT_NPMAX 128:
+// 12 warps = 4 TMEM lane quadrants x 3 column groups, one CTA per SM, all of
+// TMEM and ~207 KB of shared memory) and a small one for subgraphs with
+// npad <= 64 (GB_SPLIT_NPMAX 64: 8 warps, 256 TMEM columns, ~106 KB), which
+// runs two CTAs per SM so that one CTA's staging overlaps the other's MMAs.
+#ifndef GB_SPLIT_NPMAX
+#define GB_SPLIT_NPMAX 128
+#endif
+// GB_SPLIT_LIST: the launch walks a list of subgraphs (one size class) rather
+// than all of them.  The 128-column configuration is built both ways: with
+// the list, the same kernel measured 5% slower on the water boxes (code
+// layout; the per-subgraph work is identical), so it is used only when the
+// small class is in use.
+#ifndef GB_SPLIT_LIST
+#define GB_SPLIT_LIST 0
+#endif
+#if GB_SPLIT_NPMAX == 128 && !GB_SPLIT_LIST
+#define GB_SPLIT_THREADS 384
+#define GB_SPLIT_MINB 1
+#define GB_SPLIT_KERNEL k_fermi_split
+#define GB_SPLIT_LAUNCH launch_split_pass
+#elif GB_SPLIT_NPMAX == 128
+#define GB_SPLIT_THREADS 384
+#define GB_SPLIT_MINB 1
+#define GB_SPLIT_KERNEL k_fermi_split_listed
+#define GB_SPLIT_LAUNCH launch_split_pass_listed
+#elif GB_SPLIT_NPMAX == 64 && GB_SPLIT_LIST
+#define GB_SPLIT_THREADS 256
+#define GB_SPLIT_MINB 2
+#define GB_SPLIT_KERNEL k_fermi_split_small
+#define GB_SPLIT_LAUNCH launch_split_pass_small
+#else
+#error "GB_SPLIT_NPMAX must be 128, or 64 with GB_SPLIT_LIST"
+#endif
+constexpr int THREADS = GB_SPLIT_THREADS;
 constexpr int GROUPS = THREADS / 128;
-constexpr int NMAX = GB_SPLIT_MAX_N;
+constexpr int NMAX = GB_SPLIT_MAX_N;  // rows (TMEM lanes, M of every MMA)
+constexpr int NPMAX = GB_SPLIT_NPMAX; // largest npad (columns) of this configuration
 constexpr int REFINE_ROUNDS = 1;  // refinement rounds of the final step (the tensor-core
                                   // inverse as preconditioner leaves ~1e-14 after one)
-constexpr uint32_t HALF_BYTES = NMAX * NMAX * 2;  // one 16-bit part
+constexpr uint32_t HALF_BYTES = NMAX * NPMAX * 2;  // one 16-bit part (128 rows x npad columns)
 constexpr uint32_t STAGE_BYTES = 2 * HALF_BYTES;   // hi + lo
 constexpr int NSTAGE = 3;
 constexpr uint32_t LBO = 128 * (NMAX / 8);         // next 8-column group (K direction)
 constexpr uint32_t SBO = 128;                      // next 8-row group (M/N direction)
-constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t TMEM_COLS = 4 * NPMAX;  // Z, X, P (2 npad)
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 constexpr float STAGE_SCALE = 4096.f;               // staged operand = 2^12 x value
 constexpr float TMEM_SCALE = 16777216.f;            // TMEM word = 2^24 x value
@@ -853,6 +888,10 @@ struct Kernel {
     __device__ void diag_max() {
         if (grp != 0) return;
         const uint32_t cb = (uint32_t)(row & ~31);
+        if ((int)cb >= npad) {  // a warp of padding rows: its 32-column window may lie past the
+            if ((threadIdx.x & 31) == 0) c.wred[threadIdx.x >> 5] = 0.f;  // TMEM allocation
+            return;
+        }
         float u[16], w[16], u2[16], w2[16];
         tmem_ld16x2(col(pl) + lane_off + cb, col(pl) + lane_off + cb + 16, u, w);
         tmem_ld16x2(col(pr) + lane_off + cb, col(pr) + lane_off + cb + 16, u2, w2);
@@ -887,7 +926,7 @@ struct Kernel {
     // 8-column units as in combine (unit u to column group u mod 3); all of a
     // thread's global loads are issued before the first conversion.
     __device__ void stage_dense(const float* blk, float scale, bool use_diag, float dscale, int sg) {
-        constexpr int MAXU = (NMAX / 8 + GROUPS - 1) / GROUPS;
+        constexpr int MAXU = (NPMAX / 8 + GROUPS - 1) / GROUPS;
         const float k = scale * STAGE_SCALE;
         const bool has_diag = use_diag && row < n;
         const float dv = has_diag ? c.dg[row] * dscale * STAGE_SCALE : 0.f;
@@ -925,7 +964,7 @@ struct Kernel {
     }
 };
 
-__global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
+__global__ void __launch_bounds__(THREADS, GB_SPLIT_MINB) GB_SPLIT_KERNEL(PassArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     Ctl& c = *(Ctl*)(smem + NSTAGE * STAGE_BYTES);
@@ -952,7 +991,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
     fence_after();
     K.tbase = c.tmem_base;
 
+    // this launch's subgraphs: a size class's list, or all of them
+#if GB_SPLIT_LIST
+    const int32_t nwork = *a.work_n;
+    for (int32_t j = blockIdx.x; j < nwork && c.abort == 0; j += gridDim.x) {
+        const int32_t i = a.work[j];
+#else
     for (int32_t i = blockIdx.x; i < a.n_sub && c.abort == 0; i += gridDim.x) {
+#endif
         const int64_t s0 = a.sub_ptr[i];
         const int n = (int)(a.sub_ptr[i + 1] - s0);
         const int64_t c0 = a.core_ptr[i], c1 = a.core_ptr[i + 1];
@@ -962,7 +1008,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
             c.cpos[e] = a.core_pos[c0 + e];
             c.ocol[e] = a.col_ptr[a.core_idx[c0 + e]];
         }
+#if GB_SPLIT_LIST
+        if (j + (int32_t)gridDim.x < nwork) K.prefetch_blocks(a.work[j + gridDim.x]);
+#else
         K.prefetch_blocks(i + (int32_t)gridDim.x);
+#endif
         // the subgraph's scalars, once (FP64 is narrow on this part): step
         // count s, and sigma_r = 2^-k with (beta / 2) sigma max row sum |h1_r| <= 1
         if (threadIdx.x == 0) c.s = recursion_steps(a.beta, a.mu, a.eps_lo[i], a.eps_hi[i], a.min_steps);
@@ -983,7 +1033,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
         __syncthreads();
         // the response state Z1 of the subgraph in flight: this CTA's scratch
         // (rewritten every step, so it stays in L2)
-        uint8_t* z1base = (uint8_t*)(a.z1pool + (size_t)blockIdx.x * (a.m > 0 ? a.m : 1) * NMAX * NMAX);
+        uint8_t* z1base = (uint8_t*)a.z1pool + (size_t)blockIdx.x * (a.m > 0 ? a.m : 1) * STAGE_BYTES;
 
         // ---- Taylor start: Q = x0^2, T = I - Q/3 + 2 Q^2/15 (X region: Q, Z region: T) ----
         const float* hb = a.hblk + a.boff[i];
@@ -1071,8 +1121,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
             if (!(ok = K.gemm(2, 0))) break;                                       // P = W / 2 = X Z
             if (last) {
                 // ---- the last doubling redone on the core columns (CUDA cores) ----
-                if (ncore <= 8) K.refine_core<8>(K.zc, K.xc, TMEM_INV, ncore);
-                else K.refine_core<16>(K.zc, K.xc, TMEM_INV, ncore);
+                // (the small configuration's two slots hold the scratch of 8 columns)
+                if (ncore <= 8 || NPMAX < 128) K.refine_core<8>(K.zc, K.xc, TMEM_INV, ncore);
+                else K.refine_core<NPMAX < 128 ? 8 : 16>(K.zc, K.xc, TMEM_INV, ncore);
                 if (a.m > 0) K.combine(K.Pk(2.f), K.none(), 0.f, -1, 0, nullptr);  // S0 = W
             } else {
                 K.combine(K.Pk(2.f), K.none(), 0.f, K.zc, 0, nullptr);             // Z region = W (next Z), S0 = W
@@ -1134,6 +1185,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_fermi_split(PassArgs a) {
                      : "memory");
 }
 
+#if GB_SPLIT_NPMAX == 128 && !GB_SPLIT_LIST
 // Dense principal submatrices beta h^(i) = beta H[S_i, S_i] and beta h1_r^(i)
 // (FP32 in column groups of four, zero padding to npad), the FP64 diagonal of
 // h^(i), one block per subgraph, one warp per row.  Also the Gershgorin
@@ -1242,24 +1294,33 @@ __global__ void __launch_bounds__(256) k_gather_dense(PassArgs a, float* hblk, d
     }
 }
 
+#endif  // GB_SPLIT_NPMAX == 128
+
 }  // namespace
 
+#if GB_SPLIT_NPMAX == 128 && !GB_SPLIT_LIST
 int launch_split_gather(gb_handle* h, const PassArgs& a, float* hblk, double* hdiag) {
     const int grid = a.n_sub < 152 * 8 ? a.n_sub : 152 * 8;
     GB_LAUNCH(h, k_gather_dense, grid, 256, 0, a, hblk, hdiag);
     return GB_OK;
 }
 
-int launch_split_pass(gb_handle* h, const PassArgs& a) {
+#endif
+
+int GB_SPLIT_LAUNCH(gb_handle* h, const PassArgs& a) {
     static bool configured = false;
     if (!configured) {
-        GB_CUDA(cudaFuncSetAttribute(k_fermi_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+        GB_CUDA(cudaFuncSetAttribute(GB_SPLIT_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
         configured = true;
     }
     int sms = 0;
     GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-    int grid = a.n_sub < sms ? a.n_sub : sms;
-    if (grid > GB_SPLIT_MAX_CTAS) grid = GB_SPLIT_MAX_CTAS;
-    GB_LAUNCH(h, k_fermi_split, grid, THREADS, SMEM_BYTES, a);
+    // persistent: GB_SPLIT_MINB CTAs per SM, within the response scratch
+    // (min(n_sub, GB_SPLIT_MAX_CTAS) x 64 KB per RHS; a CTA takes STAGE_BYTES)
+    const int64_t cap = (int64_t)(a.n_sub < GB_SPLIT_MAX_CTAS ? a.n_sub : GB_SPLIT_MAX_CTAS) * 65536 / STAGE_BYTES;
+    int64_t grid = (int64_t)GB_SPLIT_MINB * sms;
+    if (grid > a.n_sub) grid = a.n_sub;
+    if (grid > cap) grid = cap;
+    GB_LAUNCH(h, GB_SPLIT_KERNEL, (int)grid, THREADS, SMEM_BYTES, a);
     return GB_OK;
 }

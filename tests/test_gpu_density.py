@@ -273,3 +273,75 @@ def test_error_statuses(gb):
     R = gb.density_and_response(Hd, H1d, kT, system.n_electrons, P, mu0=-20.0, max_newton=1,
                                 raise_on_error=False)
     assert R.status == 5
+
+
+@pytest.mark.parametrize("small", [16, 32, 64])
+def test_small_configuration(gb, small):
+    # subgraphs with round16(|S_i|) <= small run in the two-CTAs-per-SM
+    # configuration (8 warps, 256 TMEM columns): parity with the oracle and
+    # with the 128-column configuration alone (same arithmetic per element;
+    # only the refinement's partial sums are grouped differently)
+    Hc, H1c = _random_system(400, 7, density=0.012)
+    n = Hc.n
+    rng = np.random.default_rng(8)
+    block = rng.integers(1, 10, size=n)
+    groups = np.repeat(np.arange(n), block)[:n].astype(np.int32)
+    groups = np.unique(groups, return_inverse=True)[1].astype(np.int32)
+    adj = o_graph(n, Hc.indptr, Hc.indices, Hc.data, 0.0)
+    part = o_part(adj, groups)
+    npads = (part.sizes() + 15) // 16 * 16
+    assert (npads <= small).any() and (npads > small).any()
+    kT, ne = 0.3, 2 * 150.0
+    ref = oracle_graph(Hc, [H1c], kT, ne / 2, part)
+    Hd, H1d = to_device(Hc), [to_device(H1c)]
+    P = gb.partition(gb.graph_build(Hd, 0.0), torch.as_tensor(groups))
+    R0 = gb.density_and_response(Hd, H1d, kT, ne, P, precision="fp16x3", mu0=ref.mu)
+    R1 = gb.density_and_response(Hd, H1d, kT, ne, P, precision="fp16x3", mu0=ref.mu, split_small_npad=small)
+    eD, eD1 = max_abs_block_error(R1, ref, part)
+    d0 = (R1.D.val - R0.D.val).abs().max().item()
+    d1 = (R1.D1[0].val - R0.D1[0].val).abs().max().item()
+    print(f"small<={small}: {(npads <= small).sum()} of {len(npads)} subgraphs, max|dD|={eD:.2e} "
+          f"max|dD1|={eD1:.2e}, vs 128-column only {d0:.1e} {d1:.1e}")
+    assert eD <= TOL["fp16x3"] and eD1 <= TOL["fp16x3"]
+    assert d0 <= 1e-6 and d1 <= 1e-6
+
+
+def test_small_configuration_argument(gb):
+    wl, system, h1, kT, part, Hd, H1d, P = _setup(gb, "water64")
+    for bad in (8, 40, 80, -16):
+        with pytest.raises(gb.GbError):
+            gb.density_and_response(Hd, H1d, kT, system.n_electrons, P, precision="fp16x3",
+                                    split_small_npad=bad)
+
+
+def test_plan_autotune(gb):
+    # size bins -> configuration: a timing table over the candidate thresholds,
+    # a choice among them, the handle's cache on a repeated call, and a
+    # density call with the chosen threshold at the oracle's accuracy
+    Hc, H1c = _random_system(400, 7, density=0.012)
+    n = Hc.n
+    rng = np.random.default_rng(8)
+    block = rng.integers(1, 10, size=n)
+    groups = np.repeat(np.arange(n), block)[:n].astype(np.int32)
+    groups = np.unique(groups, return_inverse=True)[1].astype(np.int32)
+    adj = o_graph(n, Hc.indptr, Hc.indices, Hc.data, 0.0)
+    part = o_part(adj, groups)
+    kT, ne = 0.3, 2 * 150.0
+    ref = oracle_graph(Hc, [H1c], kT, ne / 2, part)
+    Hd, H1d = to_device(Hc), [to_device(H1c)]
+    P = gb.partition(gb.graph_build(Hd, 0.0), torch.as_tensor(groups))
+    h = gb.Handle(device=Hd.ptr.device)
+    plan = gb.plan_autotune(Hd, H1d, kT, ne, P, ref.mu, handle=h)
+    print(plan)
+    npads = (part.sizes() + 15) // 16
+    assert plan["bin_count"] == [int((npads == k + 1).sum()) for k in range(8)]
+    assert plan["candidates"][0] == 0 and plan["split_small_npad"] in plan["candidates"]
+    assert all(t > 0 for t in plan["pass_ms"]) and not plan["cached"]
+    again = gb.plan_autotune(Hd, H1d, kT, ne, P, ref.mu, handle=h)
+    assert again["cached"] and again["split_small_npad"] == plan["split_small_npad"]
+    R = gb.density_and_response(Hd, H1d, kT, ne, P, precision="fp16x3", mu0=ref.mu + 0.1,
+                                split_small_npad=plan["split_small_npad"], handle=h)
+    eD, eD1 = max_abs_block_error(R, ref, part)
+    assert eD <= TOL["fp16x3"] and eD1 <= TOL["fp16x3"]
+    with pytest.raises(ValueError):
+        gb.plan_autotune(Hd, H1d, kT, ne, P, ref.mu, precision="fp64", handle=h)
