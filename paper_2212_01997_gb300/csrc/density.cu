@@ -675,9 +675,10 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
     GB_LAUNCH(h, k_reduce, 1, REDUCE_THREADS, sizeof(double) * (stride + 2) * REDUCE_THREADS, n_sub, stride, (const double*)L.tr, (const double*)L.eps_lo,
               (const double*)L.eps_hi, L.sums, L.bounds);
     double bounds[2];
-    GB_TRY(read_f64(h, L.bounds, bounds, 2));
     int herr = 0;
-    GB_TRY(read_i32(h, L.err, &herr));
+    GB_CUDA(cudaMemcpyAsync(bounds, L.bounds, sizeof(bounds), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaMemcpyAsync(&herr, L.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaStreamSynchronize(st));  // one round trip for both
     if (herr) return herr;
 
     // mu: Newton-Raphson on the core traces (Eq. NewtonRaphson), safeguarded
@@ -717,13 +718,14 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
         GB_CUDA(cudaEventRecord(ev1, st));
         GB_LAUNCH(h, k_reduce, 1, REDUCE_THREADS, sizeof(double) * (stride + 2) * REDUCE_THREADS, n_sub, stride, (const double*)L.tr,
                   (const double*)L.eps_lo, (const double*)L.eps_hi, L.sums, L.bounds);
-        GB_TRY(read_f64(h, L.sums, sums, stride));
+        GB_CUDA(cudaMemcpyAsync(sums, L.sums, sizeof(double) * stride, cudaMemcpyDeviceToHost, st));
+        GB_CUDA(cudaMemcpyAsync(&herr, L.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GB_CUDA(cudaStreamSynchronize(st));  // one round trip per pass
         {
             float ms = 0.f;
             GB_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
             kernel_ms += ms;
         }
-        GB_TRY(read_i32(h, L.err, &herr));
         if (herr) return herr;
         if (!isfinite(sums[TR_D]) || !isfinite(sums[TR_DD])) return GB_ERR_NAN;
         const double resid = sums[TR_D] - n_occ;
@@ -770,9 +772,10 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
             GB_CUDA(cudaStreamSynchronize(st));
             for (int32_t i = 0; i < n_sub; ++i) max_steps = hs[i] > max_steps ? hs[i] : max_steps;
             delete[] hs;
+        } else {
+            GB_CUDA(cudaStreamSynchronize(st));
         }
     }
-    GB_CUDA(cudaStreamSynchronize(st));
     if (rep) {
         rep->passes = passes > o.max_newton ? o.max_newton : passes;
         rep->max_steps = max_steps;

@@ -218,8 +218,9 @@ extern "C" int gb_partition(gb_handle* h, const gb_graph* G, const int32_t* grou
     int64_t sub_nnz = 0;
     int32_t stats[3] = {0, 0, 0};
     unsigned long long out_nnz = 0;
-    GB_TRY(read_i64(h, P->sub_ptr + n_sub, &sub_nnz));
-    GB_TRY(read_i32(h, L.err, stats, 3));
+    // one round trip for the three read-backs
+    GB_CUDA(cudaMemcpyAsync(&sub_nnz, P->sub_ptr + n_sub, sizeof(sub_nnz), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaMemcpyAsync(stats, L.err, sizeof(stats), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaMemcpyAsync(&out_nnz, L.out_nnz, sizeof(out_nnz), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
     P->sub_nnz = sub_nnz;
@@ -479,8 +480,9 @@ extern "C" int gb_partition_noalloc(void* stream, const gb_graph* G, const int32
     int64_t sub_nnz = 0;
     int32_t stats[3] = {0, 0, 0};
     unsigned long long out_nnz = 0;
-    GB_TRY(read_i64(h, P->sub_ptr + n_sub, &sub_nnz));
-    GB_TRY(read_i32(h, L.err, stats, 3));
+    // one round trip for the three read-backs
+    GB_CUDA(cudaMemcpyAsync(&sub_nnz, P->sub_ptr + n_sub, sizeof(sub_nnz), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaMemcpyAsync(stats, L.err, sizeof(stats), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaMemcpyAsync(&out_nnz, L.out_nnz, sizeof(out_nnz), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
     P->sub_nnz = sub_nnz;
