@@ -22,9 +22,10 @@
 // (the response is linear in h1; d1_lambda is unscaled by 1/sigma at the end),
 // which bounds every response matrix by O(1).
 //
-// Resources per CTA: TMEM 512 columns holding Z and X (FP32, npad columns
-// each) and P (2 npad); shared memory = three staged operands (128 rows, hi
-// and lo parts, 64 KB each) laid out K-major in 8x8 core matrices without
+// Resources per CTA (128-column configuration; the small one halves the
+// columns): TMEM 4 NPMAX columns holding Z and X (FP32, npad columns each) and
+// P (2 npad); shared memory = three staged operands (128 rows, hi and lo parts,
+// NPMAX x 512 bytes each) laid out K-major in 8x8 core matrices without
 // swizzle: element (r, k) of the hi part at byte
 // (k/8)*2048 + (r/8)*128 + (r%8)*16 + (k%8)*2, the lo part npad*256 bytes on.
 //
@@ -762,6 +763,8 @@ struct Kernel {
     // 2 (I + Z^2)^-1 Z e_c by iterative refinement with the tensor-core
     // inverse X as preconditioner,  w <- w + X (2 z - w - Z (Z w)),  every
     // product rounded to nearest and every sum carried as a float pair.  The
+    // start w0 = 2 X Z e_c is the tensor-core product P = X Z of the step
+    // (P must hold it on entry).  The
     // saturated occupations (and Tr_c d) then carry no accumulation bias.
     // Writes d = (I - Z_s)/2 on the core columns and its core diagonal terms.
     // Scratch: staged operands S0 and S1 (free at this point).  All threads.
@@ -785,20 +788,18 @@ struct Kernel {
             const int nc = min(NC, ncore - b0);
             float x[NC];
             if (grp == 0) {
-                float zv[NC];
+                float zv[NC], pl_[NC], pr_[NC];
                 tmem_ld_cols<NC>(col(zs) + lane_off, c.cpos + b0, nc, zv);
+                // w0 = 2 X z: the tensor-core product P = X Z on these columns
+                // (its error is contracted by ~|I - X (I + Z^2)| in the round below)
+                tmem_ld_cols<NC>(col(pl) + lane_off, c.cpos + b0, nc, pl_);
+                tmem_ld_cols<NC>(col(pr) + lane_off, c.cpos + b0, nc, pr_);
 #pragma unroll
                 for (int cc = 0; cc < NC; ++cc) x[cc] = (row < n && cc < nc) ? zv[cc] * zsc : 0.f;
                 put_row<NC>(Vz, x);
-            }
-            __syncthreads();
-            rowvec<NC>(xs, TMEM_INV, Vz, P);                                   // X z
-            __syncthreads();
-            if (grp == 0) {
 #pragma unroll
                 for (int cc = 0; cc < NC; ++cc) {
-                    FF w0 = psum(cc);
-                    w0 = (live && cc < nc) ? FF{2.f * w0.hi, 2.f * w0.lo} : FF{0.f, 0.f};
+                    const FF w0 = (live && cc < nc) ? FF{2.f * (pl_[cc] + pr_[cc]) * zsc, 0.f} : FF{0.f, 0.f};
                     Wd[cc * NMAX + row] = w0;
                     x[cc] = w0.hi;
                 }
