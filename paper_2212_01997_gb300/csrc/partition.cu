@@ -157,8 +157,31 @@ extern "C" size_t gb_partition_workspace_size(int32_t n, int64_t nnz_g, int32_t 
     return a.used();
 }
 
-extern "C" int gb_partition(gb_handle* h, const gb_graph* G, const int32_t* group, int32_t n_groups,
-                            int32_t target_core_size, gb_part* P) {
+namespace {
+
+// The subgraph rows S_i of a partition whose cores, sizes and offsets are
+// set (the last pass of gb_partition).  The layout is the one partition_impl
+// used for these arguments: the workspace arena is laid out the same way.
+int partition_fill(gb_handle* h, const gb_graph* G, int32_t n_groups, gb_part* P) {
+    const int32_t n = G->n;
+    Arena a(h->ws, h->ws_bytes);
+    PartLayout L = layout_part(a, n, n_groups);
+    const size_t smem = sizeof(uint32_t) * ((n + 31) / 32);
+    const int64_t n_sub = P->n_sub;
+    const int grid = (int)(n_sub < 152 * 16 ? n_sub : 152 * 16);
+    if (n_sub > 0)
+        GB_LAUNCH(h, k_subgraphs, grid, SUB_THREADS, smem, n, (int32_t)n_sub, G->ptr, G->idx,
+                  (const int64_t*)P->core_ptr, P->core_idx, (int64_t*)nullptr,
+                  (const int64_t*)P->sub_ptr, P->sub_idx, P->core_pos, 1, L.err + 1);
+    GB_CUDA(cudaStreamSynchronize(h->stream));
+    return GB_OK;
+}
+
+// gb_partition; with fill = false it stops before writing the subgraph rows
+// (sizes, offsets, cores and statistics are set), for the capped partition's
+// levels that are decided from sizes alone.
+int partition_impl(gb_handle* h, const gb_graph* G, const int32_t* group, int32_t n_groups,
+                   int32_t target_core_size, gb_part* P, bool fill) {
     if (!h || !G || !P) return GB_ERR_ARG;
     const int32_t n = G->n;
     if (n <= 0 || !G->ptr || (G->nnz > 0 && !G->idx)) return GB_ERR_ARG;
@@ -228,11 +251,15 @@ extern "C" int gb_partition(gb_handle* h, const gb_graph* G, const int32_t* grou
     P->max_core = stats[2];
     P->out_nnz = (int64_t)out_nnz;
     if (sub_nnz > P->sub_capacity) return GB_ERR_CAPACITY;
-    GB_LAUNCH(h, k_subgraphs, grid, SUB_THREADS, smem, n, (int32_t)n_sub, G->ptr, G->idx,
-              (const int64_t*)P->core_ptr, P->core_idx, (int64_t*)nullptr,
-              (const int64_t*)P->sub_ptr, P->sub_idx, P->core_pos, 1, L.err + 1);
-    GB_CUDA(cudaStreamSynchronize(s));
-    return GB_OK;
+    if (!fill) return GB_OK;
+    return partition_fill(h, G, n_groups, P);
+}
+
+}  // namespace
+
+extern "C" int gb_partition(gb_handle* h, const gb_graph* G, const int32_t* group, int32_t n_groups,
+                            int32_t target_core_size, gb_part* P) {
+    return partition_impl(h, G, group, n_groups, target_core_size, P, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -343,24 +370,35 @@ extern "C" int gb_partition_capped(gb_handle* h, const gb_graph* G, const int32_
         return GB_ERR_WORKSPACE;
     }
     int64_t launches = 0;
-    // level 0: one core per group
-    int st = gb_partition(h, G, group, n_groups, 0, P);
+    // level 0: one core per group (sizes only: the rows are written once a
+    // level is final)
+    int st = partition_impl(h, G, group, n_groups, 0, P, false);
     launches += h->launches;
     if (st != GB_OK && st != GB_ERR_CAPACITY) return st;
     // level 1: oversize group cores -> one core per subgroup
     int more = 0;
     GB_TRY(cap_level(h, P, group, n_groups, subgroup, n_subgroups, max_sub, L, L.key1, &launches, &more));
     if (!more) {
+        if (st == GB_OK) {
+            h->launches = 0;
+            st = partition_fill(h, G, n_groups, P);
+            launches += h->launches;
+        }
         h->launches = launches;
         return st;
     }
     const int32_t n_keys1 = n_groups + n_subgroups;
-    st = gb_partition(h, G, L.key1, n_keys1, 0, P);
+    st = partition_impl(h, G, L.key1, n_keys1, 0, P, false);
     launches += h->launches;
     if (st != GB_OK && st != GB_ERR_CAPACITY) return st;
     // level 2: oversize subgroup cores -> one core per vertex
     GB_TRY(cap_level(h, P, L.key1, n_keys1, nullptr, 0, max_sub, L, L.key2, &launches, &more));
     if (!more) {
+        if (st == GB_OK) {
+            h->launches = 0;
+            st = partition_fill(h, G, n_keys1, P);
+            launches += h->launches;
+        }
         h->launches = launches;
         return st;
     }
