@@ -11,7 +11,8 @@
 //
 // Kernels: count both directions of every surviving entry, prefix-sum,
 // scatter, then one block per row marks its neighbours in a shared bitmap and
-// reads them back in ascending order (deterministic, duplicate-free).
+// reads them back in ascending order (deterministic, duplicate-free) over the
+// front of the row's own edge list; a copy moves the rows to their offsets.
 #include "bitset.cuh"
 #include "common.cuh"
 
@@ -80,6 +81,21 @@ __global__ void k_row_unique(int32_t n, const int64_t* off, const int32_t* edges
         __syncthreads();
         int64_t c = bitmap_compact(words, W, out_idx ? out_idx + out_ptr[i] : nullptr, scan, base);
         if (threadIdx.x == 0 && count) count[i] = c;
+    }
+}
+
+// Rows of a compressed list moved to their final offsets: row i's
+// dst_ptr[i + 1] - dst_ptr[i] entries from src + src_off[i].  A warp per row.
+__global__ void k_copy_rows(int32_t n, const int64_t* src_off, const int32_t* src, const int64_t* dst_ptr,
+                            int32_t* dst) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < n; i += nw) {
+        const int64_t len = dst_ptr[i + 1] - dst_ptr[i];
+        const int32_t* a = src + src_off[i];
+        int32_t* b = dst + dst_ptr[i];
+        for (int64_t e = lane; e < len; e += 32) b[e] = a[e];
     }
 }
 
@@ -190,10 +206,11 @@ extern "C" int gb_graph_build(gb_handle* h, const gb_csr* H, const gb_csc* D_pre
     GB_CUDA(cudaFuncSetAttribute(k_row_unique, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     GB_CUDA(cudaFuncSetAttribute(k_row_paths2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int rg = row_grid(n);
-    // unique neighbour counts of the symmetrised graph
+    // unique neighbour counts of the symmetrised graph; each row's sorted
+    // unique list is written in place over the front of its edge list
     GB_CUDA(cudaMemsetAsync(L.ucnt + n, 0, sizeof(int64_t), s));
     GB_LAUNCH(h, k_row_unique, rg, ROW_THREADS, smem, n, (const int64_t*)L.cnt,
-              (const int32_t*)L.edges, L.ucnt, (const int64_t*)nullptr, (int32_t*)nullptr);
+              (const int32_t*)L.edges, L.ucnt, (const int64_t*)L.cnt, L.edges);
     GB_TRY(exclusive_scan_i64(h, L.ucnt, L.ucnt, n + 1, L.scan_tmp));
 
     if (!paths2) {
@@ -202,14 +219,14 @@ extern "C" int gb_graph_build(gb_handle* h, const gb_csr* H, const gb_csc* D_pre
         G->nnz = total;
         if (total > G->capacity) return GB_ERR_CAPACITY;
         GB_CUDA(cudaMemcpyAsync(G->ptr, L.ucnt, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
-        GB_LAUNCH(h, k_row_unique, rg, ROW_THREADS, smem, n, (const int64_t*)L.cnt,
-                  (const int32_t*)L.edges, (int64_t*)nullptr, (const int64_t*)L.ucnt, G->idx);
+        GB_LAUNCH(h, k_copy_rows, row_grid(n), ROW_THREADS, 0, n, (const int64_t*)L.cnt,
+                  (const int32_t*)L.edges, (const int64_t*)L.ucnt, G->idx);
         GB_CUDA(cudaStreamSynchronize(s));
         return GB_OK;
     }
     // base graph materialised, then E U E^2
-    GB_LAUNCH(h, k_row_unique, rg, ROW_THREADS, smem, n, (const int64_t*)L.cnt,
-              (const int32_t*)L.edges, (int64_t*)nullptr, (const int64_t*)L.ucnt, L.base);
+    GB_LAUNCH(h, k_copy_rows, row_grid(n), ROW_THREADS, 0, n, (const int64_t*)L.cnt,
+              (const int32_t*)L.edges, (const int64_t*)L.ucnt, L.base);
     GB_CUDA(cudaMemsetAsync(L.p2cnt + n, 0, sizeof(int64_t), s));
     GB_LAUNCH(h, k_row_paths2, rg, ROW_THREADS, smem, n, (const int64_t*)L.ucnt,
               (const int32_t*)L.base, L.p2cnt, (const int64_t*)nullptr, (int32_t*)nullptr);
