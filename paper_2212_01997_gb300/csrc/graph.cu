@@ -13,6 +13,8 @@
 // scatter, then one block per row marks its neighbours in a shared bitmap and
 // reads them back in ascending order (deterministic, duplicate-free) over the
 // front of the row's own edge list; a copy moves the rows to their offsets.
+#include <string.h>
+
 #include "bitset.cuh"
 #include "common.cuh"
 
@@ -20,39 +22,65 @@ namespace {
 
 constexpr int ROW_THREADS = 256;
 
-// One thread per row of a compressed matrix (CSR rows or CSC columns; the
-// pair (major, minor) is emitted both ways, so orientation does not matter).
+// |v| > tau on the bit patterns: for non-negative doubles the IEEE order is the
+// integer order of the bits (tau >= 0 is checked on entry).  NaN bits lie above
+// those of infinity and never pass.  Keeps the graph build off the narrow FP64
+// pipe.
+__device__ __forceinline__ bool above_tau(double v, unsigned long long tau_bits, bool& nan) {
+    const unsigned long long a = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+    nan = a > 0x7ff0000000000000ull;
+    return !nan && a > tau_bits;
+}
+
+// A warp per row of a compressed matrix (CSR rows or CSC columns; the pair
+// (major, minor) is emitted both ways, so orientation does not matter).
 __global__ void k_edge_count(int32_t n, const int64_t* ptr, const int32_t* idx, const double* val,
-                             double tau, int64_t* cnt, int* err) {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+                             unsigned long long tau_bits, int64_t* cnt, int* err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
-    for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
-        int32_t j = idx[e];
+    int own = 0;
+    for (int64_t e = ptr[i] + lane; e < ptr[i + 1]; e += 32) {
+        const int32_t j = idx[e];
         if (j < 0 || j >= n) {
             set_error(err, GB_ERR_ARG);
             continue;
         }
-        double v = val[e];
-        if (!(v == v)) set_error(err, GB_ERR_NAN);
-        if (j != i && fabs(v) > tau) {
-            atomicAdd((unsigned long long*)&cnt[i], 1ull);
+        bool nan;
+        const bool keep = above_tau(val[e], tau_bits, nan) && j != i;
+        if (nan) set_error(err, GB_ERR_NAN);
+        if (keep) {
+            ++own;
             atomicAdd((unsigned long long*)&cnt[j], 1ull);
         }
     }
+    for (int o = 16; o > 0; o >>= 1) own += __shfl_xor_sync(0xffffffffu, own, o);
+    if (lane == 0 && own) atomicAdd((unsigned long long*)&cnt[i], (unsigned long long)own);
 }
 
 __global__ void k_edge_fill(int32_t n, const int64_t* ptr, const int32_t* idx, const double* val,
-                            double tau, const int64_t* off, int64_t* cursor, int32_t* edges) {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+                            unsigned long long tau_bits, const int64_t* off, int64_t* cursor, int32_t* edges) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
-    for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
-        int32_t j = idx[e];
-        if (j < 0 || j >= n) continue;
-        if (j != i && fabs(val[e]) > tau) {
-            int64_t a = atomicAdd((unsigned long long*)&cursor[i], 1ull);
-            int64_t b = atomicAdd((unsigned long long*)&cursor[j], 1ull);
+    for (int64_t e0 = ptr[i]; e0 < ptr[i + 1]; e0 += 32) {
+        const int64_t e = e0 + lane;
+        bool keep = false;
+        int32_t j = -1;
+        if (e < ptr[i + 1]) {
+            j = idx[e];
+            bool nan;
+            keep = j >= 0 && j < n && j != i && above_tau(val[e], tau_bits, nan);
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, keep);
+        unsigned long long base = 0;
+        if (lane == 0 && m) base = atomicAdd((unsigned long long*)&cursor[i], (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (keep) {
+            const int64_t a = (int64_t)base + __popc(m & ((1u << lane) - 1u));
+            const int64_t b = (int64_t)atomicAdd((unsigned long long*)&cursor[j], 1ull);
             edges[off[i] + a] = j;
-            edges[off[j] + b] = i;
+            edges[off[j] + b] = (int32_t)i;
         }
     }
 }
@@ -185,22 +213,23 @@ extern "C" int gb_graph_build(gb_handle* h, const gb_csr* H, const gb_csc* D_pre
     GB_CUDA(cudaMemsetAsync(L.cnt, 0, sizeof(int64_t) * (n + 1), s));
     GB_CUDA(cudaMemsetAsync(L.cursor, 0, sizeof(int64_t) * n, s));
     GB_CUDA(cudaMemsetAsync(L.err, 0, sizeof(int) * 4, s));
-    const int tb = 256, gb = (n + tb - 1) / tb;
-    GB_LAUNCH(h, k_edge_count, gb, tb, 0, n, H->ptr, H->idx, H->val, tau, L.cnt, L.err);
+    const int tb = 256, gb = (int)(((int64_t)n * 32 + tb - 1) / tb);  // a warp per row
+    unsigned long long tb_bits = 0;
+    memcpy(&tb_bits, &tau, sizeof(tb_bits));
+    tb_bits &= 0x7fffffffffffffffull;  // tau >= 0 (or -0): its bits order like its value
+    GB_LAUNCH(h, k_edge_count, gb, tb, 0, n, H->ptr, H->idx, H->val, tb_bits, L.cnt, L.err);
     if (D_prev)
         GB_LAUNCH(h, k_edge_count, gb, tb, 0, n, (const int64_t*)D_prev->ptr,
-                  (const int32_t*)D_prev->idx, (const double*)D_prev->val, tau, L.cnt, L.err);
+                  (const int32_t*)D_prev->idx, (const double*)D_prev->val, tb_bits, L.cnt, L.err);
     GB_TRY(exclusive_scan_i64(h, L.cnt, L.cnt, n + 1, L.scan_tmp));
-    GB_LAUNCH(h, k_edge_fill, gb, tb, 0, n, H->ptr, H->idx, H->val, tau, (const int64_t*)L.cnt,
+    GB_LAUNCH(h, k_edge_fill, gb, tb, 0, n, H->ptr, H->idx, H->val, tb_bits, (const int64_t*)L.cnt,
               L.cursor, L.edges);
     if (D_prev)
         GB_LAUNCH(h, k_edge_fill, gb, tb, 0, n, (const int64_t*)D_prev->ptr,
-                  (const int32_t*)D_prev->idx, (const double*)D_prev->val, tau,
+                  (const int32_t*)D_prev->idx, (const double*)D_prev->val, tb_bits,
                   (const int64_t*)L.cnt, L.cursor, L.edges);
-    int herr = 0;
-    GB_TRY(read_i32(h, L.err, &herr));
-    if (herr) return herr;
-
+    // (the input-error flag is read back with the first count below: the
+    // kernels in between skip the entries that set it)
     const size_t smem = sizeof(uint32_t) * ((n + 31) / 32);
     if (smem > 200 * 1024) return GB_ERR_UNSUPPORTED;
     GB_CUDA(cudaFuncSetAttribute(k_row_unique, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -213,9 +242,13 @@ extern "C" int gb_graph_build(gb_handle* h, const gb_csr* H, const gb_csc* D_pre
               (const int32_t*)L.edges, L.ucnt, (const int64_t*)L.cnt, L.edges);
     GB_TRY(exclusive_scan_i64(h, L.ucnt, L.ucnt, n + 1, L.scan_tmp));
 
+    int herr = 0;
     if (!paths2) {
         int64_t total = 0;
-        GB_TRY(read_i64(h, L.ucnt + n, &total));
+        GB_CUDA(cudaMemcpyAsync(&total, L.ucnt + n, sizeof(total), cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaMemcpyAsync(&herr, L.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaStreamSynchronize(s));
+        if (herr) return herr;
         G->nnz = total;
         if (total > G->capacity) return GB_ERR_CAPACITY;
         GB_CUDA(cudaMemcpyAsync(G->ptr, L.ucnt, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
@@ -224,6 +257,8 @@ extern "C" int gb_graph_build(gb_handle* h, const gb_csr* H, const gb_csc* D_pre
         GB_CUDA(cudaStreamSynchronize(s));
         return GB_OK;
     }
+    GB_TRY(read_i32(h, L.err, &herr));
+    if (herr) return herr;
     // base graph materialised, then E U E^2
     GB_LAUNCH(h, k_copy_rows, row_grid(n), ROW_THREADS, 0, n, (const int64_t*)L.cnt,
               (const int32_t*)L.edges, (const int64_t*)L.ucnt, L.base);
