@@ -157,20 +157,26 @@ __global__ void __launch_bounds__(GERSH_THREADS) k_gershgorin(int32_t n_sub, con
     }
 }
 
-// Single-block reduction in a fixed order (deterministic): sums of the
-// per-subgraph trace slots, min of eps_lo and max of eps_hi.  Thread t owns a
-// fixed contiguous range of subgraphs and accumulates every quantity of it in
-// one sweep; the threads' partials are then combined by a fixed tree.
+// Reduction in a fixed order (deterministic): sums of the per-subgraph trace
+// slots, min of eps_lo and max of eps_hi.  Block b takes the fixed range
+// [b chunk, (b + 1) chunk) of subgraphs; within it thread t owns a fixed
+// contiguous sub-range and accumulates every quantity in one sweep, the
+// threads' partials combine by a fixed tree into partial[b][q], and
+// k_reduce_final adds the blocks' partials in block order.  (The FP64 work is
+// spread over the SMs: one block measured ~70 us a call.)
 constexpr int REDUCE_THREADS = 256;  // (stride + 2) x 256 doubles <= 30 KB of shared memory
+constexpr int REDUCE_BLOCKS = 160;
 constexpr int REDUCE_MAXQ = TR_FIXED + GB_MAX_RHS + 2;
 __global__ void __launch_bounds__(REDUCE_THREADS) k_reduce(int32_t n_sub, int32_t stride, const double* tr,
                                                            const double* eps_lo, const double* eps_hi,
-                                                           double* sums, double* bounds) {
+                                                           double* partial) {
     extern __shared__ double sh[];  // [stride + 2][REDUCE_THREADS]
     const int nq = stride + 2;
     const int t = threadIdx.x;
-    const int32_t per = (n_sub + REDUCE_THREADS - 1) / REDUCE_THREADS;
-    const int32_t i0 = min(n_sub, t * per), i1 = min(n_sub, i0 + per);
+    const int32_t chunk = (n_sub + (int32_t)gridDim.x - 1) / (int32_t)gridDim.x;
+    const int32_t b0 = min(n_sub, (int32_t)blockIdx.x * chunk), b1 = min(n_sub, b0 + chunk);
+    const int32_t per = (b1 - b0 + REDUCE_THREADS - 1) / REDUCE_THREADS;
+    const int32_t i0 = min(b1, b0 + t * per), i1 = min(b1, i0 + per);
     double v[REDUCE_MAXQ];
 #pragma unroll
     for (int k = 0; k < REDUCE_MAXQ; ++k) v[k] = 0.0;
@@ -201,10 +207,22 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_reduce(int32_t n_sub, int32_
         }
         __syncthreads();
     }
-    if (t < nq) {
-        if (t < stride) sums[t] = sh[t * REDUCE_THREADS];
-        else bounds[t - stride] = sh[t * REDUCE_THREADS];
+    if (t < nq) partial[(int64_t)blockIdx.x * nq + t] = sh[t * REDUCE_THREADS];
+}
+
+__global__ void k_reduce_final(int32_t nblocks, int32_t stride, const double* partial, double* sums,
+                               double* bounds) {
+    const int nq = stride + 2;
+    const int k = threadIdx.x;
+    if (k >= nq) return;
+    const int op = k < stride ? (k == TR_MAXW ? 2 : 0) : (k == stride ? 1 : 2);  // sum, min, max
+    double v = partial[k];
+    for (int32_t b = 1; b < nblocks; ++b) {
+        const double x = partial[(int64_t)b * nq + k];
+        v = op == 0 ? v + x : (op == 1 ? fmin(v, x) : fmax(v, x));
     }
+    if (k < stride) sums[k] = v;
+    else bounds[k - stride] = v;
 }
 
 // The subgraphs of the two size classes of the split launches, each list in
@@ -476,6 +494,7 @@ struct DensityLayout {
     int32_t* steps;     // n_sub
     double* tr;         // n_sub * (TR_FIXED + m)
     double* sums;       // TR_FIXED + m
+    double* partial;    // REDUCE_BLOCKS x (TR_FIXED + m + 2): k_reduce's per-block results
     double* bounds;     // 2
     double* d1mu_val;   // out_nnz
     int64_t* scan_tmp;
@@ -499,6 +518,7 @@ DensityLayout layout_density(Arena& ar, const gb_part* P, int32_t m, int precisi
     L.steps = ar.take<int32_t>(n_sub);
     L.tr = ar.take<double>(n_sub * (TR_FIXED + m));
     L.sums = ar.take<double>(TR_FIXED + m + 8);
+    L.partial = ar.take<double>((int64_t)REDUCE_BLOCKS * (TR_FIXED + m + 2));
     L.bounds = ar.take<double>(8);
     L.d1mu_val = ar.take<double>(P->out_nnz);
     L.scan_tmp = ar.take<int64_t>(scan_temp_count(n_sub + 1) + 64);
@@ -531,6 +551,15 @@ DensityLayout layout_density(Arena& ar, const gb_part* P, int32_t m, int precisi
 }
 
 }  // namespace
+
+// the two launches of the deterministic trace / bound reduction
+static int reduce_traces(gb_handle* h, int32_t n_sub, int32_t stride, const DensityLayout& L) {
+    const int nb = n_sub < REDUCE_BLOCKS ? n_sub : REDUCE_BLOCKS;
+    GB_LAUNCH(h, k_reduce, nb, REDUCE_THREADS, sizeof(double) * (stride + 2) * REDUCE_THREADS, n_sub, stride,
+              (const double*)L.tr, (const double*)L.eps_lo, (const double*)L.eps_hi, L.partial);
+    GB_LAUNCH(h, k_reduce_final, 1, 32, 0, nb, stride, (const double*)L.partial, L.sums, L.bounds);
+    return GB_OK;
+}
 
 extern "C" int gb_density_workspace_size(const gb_part* P, int32_t m, const gb_opts* opts,
                                          size_t* bytes) {
@@ -674,8 +703,7 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
         GB_LAUNCH(h, k_gershgorin, sub_grid, GERSH_THREADS, 0, n_sub, P->sub_ptr, P->sub_idx, H->ptr, H->idx,
                   H->val, L.eps_lo, L.eps_hi);
     }
-    GB_LAUNCH(h, k_reduce, 1, REDUCE_THREADS, sizeof(double) * (stride + 2) * REDUCE_THREADS, n_sub, stride, (const double*)L.tr, (const double*)L.eps_lo,
-              (const double*)L.eps_hi, L.sums, L.bounds);
+    GB_TRY(reduce_traces(h, n_sub, stride, L));
     double bounds[2];
     int herr = 0;
     GB_CUDA(cudaMemcpyAsync(bounds, L.bounds, sizeof(bounds), cudaMemcpyDeviceToHost, st));
@@ -718,8 +746,7 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
             GB_LAUNCH(h, k_fermi_fp64, sub_grid, FP64_THREADS, 0, a);
         }
         GB_CUDA(cudaEventRecord(ev1, st));
-        GB_LAUNCH(h, k_reduce, 1, REDUCE_THREADS, sizeof(double) * (stride + 2) * REDUCE_THREADS, n_sub, stride, (const double*)L.tr,
-                  (const double*)L.eps_lo, (const double*)L.eps_hi, L.sums, L.bounds);
+        GB_TRY(reduce_traces(h, n_sub, stride, L));
         GB_CUDA(cudaMemcpyAsync(sums, L.sums, sizeof(double) * stride, cudaMemcpyDeviceToHost, st));
         GB_CUDA(cudaMemcpyAsync(&herr, L.err, sizeof(int), cudaMemcpyDeviceToHost, st));
         GB_CUDA(cudaStreamSynchronize(st));  // one round trip per pass
