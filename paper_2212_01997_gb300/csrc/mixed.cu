@@ -924,6 +924,40 @@ struct Kernel {
     // staged operand from a gathered block beta M (FP32, column groups of four):
     // scale x blk, scale = 2^-(s+1) [x sigma] (exact power of two), and, with
     // use_diag, the diagonal dscale x c.dg (the x0 diagonal computed in FP64)
+    // Staged operand sg times 2^e in place (its hi and lo parts scale exactly
+    // unless a lo part is subnormal, ~2^-36 of the value): the same units as
+    // combine.  Every thread; the next gemm's barrier orders it.
+    __device__ void scale_staged(int sg, int e) {
+        const int nu = npad / 8;
+        for (int u = grp; u < nu; u += GROUPS) {
+            uint4* p = (uint4*)(st(sg) + elem_off(row, 8 * u));
+            uint4* q = (uint4*)((uint8_t*)p + lo_off);
+            uint4 h = *p, l = *q;
+            uint32_t* hv = (uint32_t*)&h;
+            uint32_t* lv = (uint32_t*)&l;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (fmt == 0) {
+                    const __half2 f = __float2half2_rn(ldexpf(1.f, e));
+                    __half2 a = *(__half2*)&hv[j], b = *(__half2*)&lv[j];
+                    a = __hmul2(a, f);
+                    b = __hmul2(b, f);
+                    hv[j] = *(uint32_t*)&a;
+                    lv[j] = *(uint32_t*)&b;
+                } else {
+                    const __nv_bfloat162 f = __float2bfloat162_rn(ldexpf(1.f, e));
+                    __nv_bfloat162 a = *(__nv_bfloat162*)&hv[j], b = *(__nv_bfloat162*)&lv[j];
+                    a = __hmul2(a, f);
+                    b = __hmul2(b, f);
+                    hv[j] = *(uint32_t*)&a;
+                    lv[j] = *(uint32_t*)&b;
+                }
+            }
+            *p = h;
+            *q = l;
+        }
+    }
+
     // 8-column units as in combine (unit u to column group u mod 3); all of a
     // thread's global loads are issued before the first conversion.
     __device__ void stage_dense(const float* blk, float scale, bool use_diag, float dscale, int sg) {
@@ -1047,7 +1081,7 @@ __global__ void __launch_bounds__(THREADS, GB_SPLIT_MINB) GB_SPLIT_KERNEL(PassAr
         if (k > 0) {
             s -= k;
             qscale = ldexpf(1.f, 2 * k);
-            K.stage_dense(hb, ldexpf(1.f, -(s + 1)), true, ldexpf(1.f, k), 0);  // S0 = 2^k x0
+            K.scale_staged(0, k);                                          // S0 = 2^k x0
         }
         K.combine(K.Pk(qscale), K.none(), 0.f, K.xc, 1, nullptr);          // X region = Q, S1 = Q
         if (!K.gemm(1, 1)) break;                                         // P = Q^2
