@@ -211,14 +211,17 @@ int partition_impl(gb_handle* h, const gb_graph* G, const int32_t* group, int32_
     GB_CUDA(cudaMemsetAsync(L.out_nnz, 0, sizeof(unsigned long long), s));
     const int tb = 256;
     GB_LAUNCH(h, k_group_count, (n + tb - 1) / tb, tb, 0, n, group, block, n_groups, L.gcnt, L.err);
-    int herr = 0;
-    GB_TRY(read_i32(h, L.err, &herr));
-    if (herr) return herr;
+    // (out-of-range group ids are skipped by the count and reported with the
+    // core count below: one round trip)
     GB_LAUNCH(h, k_nonempty, (n_groups + tb - 1) / tb, tb, 0, n_groups, (const int64_t*)L.gcnt, L.cidx);
     GB_CUDA(cudaMemsetAsync(L.cidx + n_groups, 0, sizeof(int64_t), s));
     GB_TRY(exclusive_scan_i64(h, L.cidx, L.cidx, n_groups + 1, L.scan_tmp));
     int64_t n_sub = 0;
-    GB_TRY(read_i64(h, L.cidx + n_groups, &n_sub));
+    int herr = 0;
+    GB_CUDA(cudaMemcpyAsync(&n_sub, L.cidx + n_groups, sizeof(n_sub), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaMemcpyAsync(&herr, L.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    if (herr) return herr;
     P->n_sub = (int32_t)n_sub;
     GB_LAUNCH(h, k_core_sizes, (n_groups + tb - 1) / tb, tb, 0, n_groups, (const int64_t*)L.gcnt,
               (const int64_t*)L.cidx, P->core_ptr);
@@ -490,14 +493,17 @@ extern "C" int gb_partition_noalloc(void* stream, const gb_graph* G, const int32
     GB_CUDA(cudaMemsetAsync(L.out_nnz, 0, sizeof(unsigned long long), s));
     const int tb = 256;
     GB_LAUNCH(h, k_group_count, (n + tb - 1) / tb, tb, 0, n, group, block, n_groups, L.gcnt, L.err);
-    int herr = 0;
-    GB_TRY(read_i32(h, L.err, &herr));
-    if (herr) return herr;
+    // (out-of-range group ids are skipped by the count and reported with the
+    // core count below: one round trip)
     GB_LAUNCH(h, k_nonempty, (n_groups + tb - 1) / tb, tb, 0, n_groups, (const int64_t*)L.gcnt, L.cidx);
     GB_CUDA(cudaMemsetAsync(L.cidx + n_groups, 0, sizeof(int64_t), s));
     GB_TRY(exclusive_scan_i64(h, L.cidx, L.cidx, n_groups + 1, L.scan_tmp));
     int64_t n_sub = 0;
-    GB_TRY(read_i64(h, L.cidx + n_groups, &n_sub));
+    int herr = 0;
+    GB_CUDA(cudaMemcpyAsync(&n_sub, L.cidx + n_groups, sizeof(n_sub), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaMemcpyAsync(&herr, L.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    if (herr) return herr;
     P->n_sub = (int32_t)n_sub;
     GB_LAUNCH(h, k_core_sizes, (n_groups + tb - 1) / tb, tb, 0, n_groups, (const int64_t*)L.gcnt,
               (const int64_t*)L.cidx, P->core_ptr);
