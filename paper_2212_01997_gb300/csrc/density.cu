@@ -500,7 +500,7 @@ struct DensityLayout {
     int64_t* scan_tmp;
     int* err;
     double* pool;       // FP64: (NBUF + m) * pool_stride
-    float* z1pool;      // split: min(n_sub, GB_SPLIT_MAX_CTAS) * m * 128 * 128 (per CTA)
+    float* z1pool;      // split: min(n_sub, GB_SPLIT_MAX_CTAS) x m x 64 KB: staged Z1 images, per CTA
     float* hblk;        // split: (1 + m) * pool_stride dense gathered blocks (FP32)
     double* hdiag;      // split: sub_nnz FP64 diagonals of h^(i)
     double* h1max;      // split: n_sub * m largest |h1| row sums

@@ -8,8 +8,9 @@
 
 constexpr int GB_MAX_RHS = 8;
 constexpr int GB_SPLIT_MAX_N = 128;  // largest subgraph of the tensor-core kernel
-// most CTAs of the persistent tensor-core kernel (one per SM); each owns one
-// FP32 response scratch of m x 128 x 128
+// sizes the response scratch of the persistent tensor-core kernels: 64 KB per
+// RHS for each of up to this many 128-column CTAs (a small-configuration CTA
+// takes 32 KB, so twice as many of those fit)
 constexpr int GB_SPLIT_MAX_CTAS = 256;
 
 // Per-subgraph trace slots (tr[i * tr_stride + k])
@@ -63,10 +64,11 @@ struct PassArgs {
     double* pool;
     const int64_t* moff;
     int64_t pool_stride;
-    // split path: FP32 response state, 128 x 128 per subgraph and RHS
+    // split path: response state Z1 of each CTA's subgraph in flight, per RHS, as
+    // a staged image (FP16 hi/lo parts in the shared-memory operand layout)
     float* z1pool;
-    // split path: gathered dense blocks beta h^(i) and beta h1_r^(i) (FP32, each
-    // rounded once from the FP64 product), npad = round16(|S_i|) rows and
+    // split path: gathered dense blocks beta h^(i) and beta h1_r^(i) (FP32:
+    // value rounded to float, times beta in FP32), npad = round16(|S_i|) rows and
     // columns, stored in column groups of four: element (r, c) at
     // ((c / 4) * npad + r) * 4 + c % 4, so a warp reading one group of 32 rows
     // reads 512 contiguous bytes.  Block b of subgraph i is at
