@@ -83,6 +83,20 @@ def max_over_ranks(x: float, world, dist, device) -> float:
     return float(t.item())
 
 
+def csc_asymmetry(n: int, ptr, idx, val) -> float:
+    """max |D_jk - D_kj| of a column-collected matrix (absent entries are 0).
+
+    The collected D is not symmetric in general: column j holds the rows of
+    its own subgraph, and row j of column k comes from another subgraph.
+    """
+    import numpy as np
+    import scipy.sparse as sp
+
+    m = sp.csc_matrix((np.asarray(val, dtype=np.float64), np.asarray(idx), np.asarray(ptr)), shape=(n, n))
+    d = (m - m.T).tocoo()
+    return float(np.abs(d.data).max()) if d.nnz else 0.0
+
+
 def whole_job_rate(units_per_rank: float, ms: float, world: int) -> float:
     """Units all ranks processed per second, timed by the slowest rank."""
     return world * units_per_rank / (ms / 1e3)
@@ -294,6 +308,11 @@ def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world,
                kernel_ms=statistics.mean(k / p for k, p in zip(k_m, pass_m)),
                flops=statistics.mean(fl_m), mean_sub=float(sizes.mean().item()))
     Dm, D1m = Rm.D.val.clone(), Rm.D1[0].val.clone()
+    try:  # diagnostic, outside the timed region
+        out["max_abs_D_minus_DT"] = csc_asymmetry(system.n_orb, Rm.D.ptr.cpu().numpy(), Rm.D.idx.cpu().numpy(),
+                                                  Dm.cpu().numpy())
+    except Exception:  # noqa: BLE001 - a diagnostic never fails the bench
+        out["max_abs_D_minus_DT"] = None
 
     if e2e_steps:
         # public API from pinned host buffers: H2D of H, H1 and D2H of D, D1
@@ -543,6 +562,7 @@ def main():
             "mixed_over_fp64": head["value"] / world / head["fp64"]["value"],
             "accuracy_vs_fp64_gpu": head["accuracy_vs_fp64_gpu"],
             "mu": head["mu"], "mu1": head["mu1"], "passes": head["passes"], "max_steps": head["max_steps"],
+            "max_abs_D_minus_DT": head.get("max_abs_D_minus_DT"),
         }
         if comp is not None:
             cwl, csys = comp["wl"], comp["system"]

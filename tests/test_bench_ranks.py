@@ -64,3 +64,22 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
         workload, warmup, steps = "water10k", 0, 0
     assert bench.run_reference(Args(), rank=1, world=2) is None
     assert capsys.readouterr().out == ""
+
+
+def test_csc_asymmetry_of_a_collected_matrix():
+    # column-collected D: column j carries its own subgraph's rows, so
+    # D_jk and D_kj come from different subgraphs (or one is absent)
+    import numpy as np
+    rng = np.random.default_rng(3)
+    n = 7
+    a = rng.normal(size=(n, n))
+    s = a + a.T
+    s[np.abs(s) < 0.5] = 0.0
+    import scipy.sparse as sp
+    m = sp.csc_matrix(s)
+    assert bench.csc_asymmetry(n, m.indptr, m.indices, m.data) == 0.0
+    t = s.copy()
+    t[1, 4] += 0.25          # one entry perturbed
+    t[5, 2], t[2, 5] = 0.75, 0.0   # one side absent
+    m2 = sp.csc_matrix(t)
+    assert abs(bench.csc_asymmetry(n, m2.indptr, m2.indices, m2.data) - max(0.25, 0.75)) < 1e-15
