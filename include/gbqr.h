@@ -115,9 +115,11 @@ typedef struct gb_opts {
     int32_t min_steps;   /* lower bound on recursion steps; <= 0 selects 6                 */
     int32_t ns_iters;    /* Newton-Schulz corrections per step; <= 0 selects 3 (FP64) / 2 */
     double tol_d;        /* accept mu when the remaining Newton step |dmu| = |Tr D - N_occ|
-                            / (dTr D / dmu) would change no element of D by more than
-                            tol_d, using |dD_jk| <= |dmu| max diag(beta d (I - d)) (d1_mu is
-                            positive semidefinite).  <= 0 selects 1e-11 (FP64) / 1e-6 (split).
+                            / (dTr D / dmu) would change no collected element of D by more
+                            than tol_d, using |dD_jk| <= |dmu| sqrt(w_jj w_kk) for the
+                            positive semidefinite w = beta d (I - d), with w_jj bounded by
+                            its largest diagonal over all rows and w_kk (k a core vertex)
+                            over the core rows.  <= 0 selects 1e-11 (FP64) / 1e-6 (split).
                             When a Newton step no longer halves the residual (trace
                             round-off floor) mu is accepted once that bound is within
                             100 tol_d (split precision) or 10 tol_d (FP64).                 */
@@ -143,7 +145,8 @@ typedef struct gb_report {
                                 summed over the products the recursion performs            */
     double pass_kernel_ms;   /* device time of the recursion kernel, summed over passes
                                 (CUDA events on the handle's stream)                       */
-    double mu_d_bound;       /* bound on the change of D the remaining mu step would make */
+    double mu_d_bound;       /* bound on the change of D the remaining mu step would make
+                                (first order; see gb_opts.tol_d)                          */
     int64_t kernel_launches; /* kernels launched by this call                             */
 } gb_report;
 
@@ -284,8 +287,10 @@ int gb_partition_noalloc(void* stream, const gb_graph* G, const int32_t* group, 
  *   rep      out, [host] report or NULL.
  * The recursion computes d = (I - Z_s)/2 with Z_s = tanh(beta (h - mu)/2) by
  * s doublings Z <- 2 Z (I + Z^2)^-1 from a Taylor start, and d1_lambda by the
- * exact derivative of the same recursion.  Split-precision modes require
- * |S_i| <= 128 (else GB_ERR_UNSUPPORTED); FP64 has no size limit.
+ * exact derivative of the same recursion.  Split-precision modes take
+ * subgraphs of up to 128 orbitals in one CTA's tensor memory and larger ones
+ * (up to 2,048 orbitals, else GB_ERR_UNSUPPORTED) in a tiled kernel whose
+ * per-CTA state lives in the workspace; FP64 has no size limit.
  * Errors: GB_ERR_ARG, GB_ERR_CAPACITY, GB_ERR_WORKSPACE, GB_ERR_MU_BRACKET,
  * GB_ERR_NO_CONVERGE (outputs hold the last pass), GB_ERR_NAN, GB_ERR_DEVICE,
  * GB_ERR_UNSUPPORTED, GB_ERR_TIMEOUT.  Synchronises the stream.

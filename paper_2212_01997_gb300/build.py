@@ -19,12 +19,14 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libgbqr.so")
-# (source, object, defines): mixed.cu is compiled twice, once per size class of
-# the split-precision kernel
+# (source, object, defines): mixed.cu is compiled three times, once per
+# configuration of the one-tile split-precision kernel; big.cu holds the tiled
+# kernel for subgraphs above 128 orbitals
 SOURCES = [("api.cu", "api", []), ("graph.cu", "graph", []), ("partition.cu", "partition", []),
            ("density.cu", "density", []), ("mixed.cu", "mixed", []),
            ("mixed.cu", "mixed_listed", ["-DGB_SPLIT_LIST=1"]),
-           ("mixed.cu", "mixed_small", ["-DGB_SPLIT_NPMAX=64", "-DGB_SPLIT_LIST=1"])]
+           ("mixed.cu", "mixed_small", ["-DGB_SPLIT_NPMAX=64", "-DGB_SPLIT_LIST=1"]),
+           ("big.cu", "big", [])]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -181,12 +181,13 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_reduce(int32_t n_sub, int32_
 #pragma unroll
     for (int k = 0; k < REDUCE_MAXQ; ++k) v[k] = 0.0;
     v[TR_MAXW] = -INFINITY;
+    v[TR_MAXWC] = -INFINITY;
     double lo = INFINITY, hi = -INFINITY;
     for (int32_t i = i0; i < i1; ++i) {
         const double* row = tr + (int64_t)i * stride;
 #pragma unroll
         for (int k = 0; k < REDUCE_MAXQ - 2; ++k) {
-            if (k < stride) v[k] = k == TR_MAXW ? fmax(v[k], row[k]) : v[k] + row[k];
+            if (k < stride) v[k] = trace_slot_is_max(k) ? fmax(v[k], row[k]) : v[k] + row[k];
         }
         lo = fmin(lo, eps_lo[i]);
         hi = fmax(hi, eps_hi[i]);
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_reduce(int32_t n_sub, int32_
         if (t < o) {
             for (int k = 0; k < nq; ++k) {
                 const double a = sh[k * REDUCE_THREADS + t], b = sh[k * REDUCE_THREADS + t + o];
-                const int op = k < stride ? (k == TR_MAXW ? 2 : 0) : (k == stride ? 1 : 2);  // sum, min, max
+                const int op = k < stride ? (trace_slot_is_max(k) ? 2 : 0) : (k == stride ? 1 : 2);  // sum, min, max
                 sh[k * REDUCE_THREADS + t] = op == 0 ? a + b : (op == 1 ? fmin(a, b) : fmax(a, b));
             }
         }
@@ -215,7 +216,7 @@ __global__ void k_reduce_final(int32_t nblocks, int32_t stride, const double* pa
     const int nq = stride + 2;
     const int k = threadIdx.x;
     if (k >= nq) return;
-    const int op = k < stride ? (k == TR_MAXW ? 2 : 0) : (k == stride ? 1 : 2);  // sum, min, max
+    const int op = k < stride ? (trace_slot_is_max(k) ? 2 : 0) : (k == stride ? 1 : 2);  // sum, min, max
     double v = partial[k];
     for (int32_t b = 1; b < nblocks; ++b) {
         const double x = partial[(int64_t)b * nq + k];
@@ -225,50 +226,53 @@ __global__ void k_reduce_final(int32_t nblocks, int32_t stride, const double* pa
     else bounds[k - stride] = v;
 }
 
-// The subgraphs of the two size classes of the split launches, each list in
-// ascending order: work[0, n0) with round16(|S_i|) > small, work[n_sub,
-// n_sub + n1) with round16(|S_i|) <= small; work_n = {n0, n1}.  One block;
-// thread t takes a fixed contiguous range, offsets by a block scan.
+// The subgraphs of the three size classes of the split launches, each list
+// in ascending order, class k at work[k n_sub, k n_sub + work_n[k]):
+// k = 0: small < round16(|S_i|) <= 128 (the 128-column configuration),
+// k = 1: round16(|S_i|) <= small (the small configuration),
+// k = 2: round16(|S_i|) > 128 (the tiled configuration).
+// One block; thread t takes a fixed contiguous range, offsets by a block scan.
 constexpr int CLASS_THREADS = 1024;
+__device__ __forceinline__ int size_class(int64_t n, int32_t small) {
+    const int64_t np = (n + 15) & ~(int64_t)15;
+    return np > GB_SPLIT_MAX_N ? 2 : (np <= small ? 1 : 0);
+}
 __global__ void __launch_bounds__(CLASS_THREADS) k_class_lists(int32_t n_sub, const int64_t* sub_ptr,
                                                                int32_t small, int32_t* work, int32_t* work_n) {
-    __shared__ int32_t wsum[2][CLASS_THREADS / 32];
+    __shared__ int32_t wsum[3][CLASS_THREADS / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int32_t per = (n_sub + CLASS_THREADS - 1) / CLASS_THREADS;
     const int32_t i0 = min(n_sub, t * per), i1 = min(n_sub, i0 + per);
-    int32_t c1 = 0;
-    for (int32_t i = i0; i < i1; ++i) c1 += (int32_t)(((sub_ptr[i + 1] - sub_ptr[i] + 15) & ~15) <= small);
-    const int32_t c0 = (i1 - i0) - c1;
-    int32_t s0 = c0, s1 = c1;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int32_t y0 = __shfl_up_sync(0xffffffffu, s0, o), y1 = __shfl_up_sync(0xffffffffu, s1, o);
-        if (lane >= o) {
-            s0 += y0;
-            s1 += y1;
+    int32_t cnt[3] = {0, 0, 0};
+    for (int32_t i = i0; i < i1; ++i) ++cnt[size_class(sub_ptr[i + 1] - sub_ptr[i], small)];
+    int32_t incl[3];
+    for (int k = 0; k < 3; ++k) {
+        int32_t v = cnt[k];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
         }
-    }
-    if (lane == 31) {
-        wsum[0][warp] = s0;
-        wsum[1][warp] = s1;
+        incl[k] = v;
+        if (lane == 31) wsum[k][warp] = v;
     }
     __syncthreads();
-    int32_t b0 = 0, b1 = 0, t0 = 0, t1 = 0;
-    for (int w = 0; w < CLASS_THREADS / 32; ++w) {
-        const int32_t v0 = wsum[0][w], v1 = wsum[1][w];
-        b0 += w < warp ? v0 : 0;
-        b1 += w < warp ? v1 : 0;
-        t0 += v0;
-        t1 += v1;
+    int32_t pos[3], tot[3];
+    for (int k = 0; k < 3; ++k) {
+        int32_t b = 0, tt = 0;
+        for (int w = 0; w < CLASS_THREADS / 32; ++w) {
+            const int32_t v = wsum[k][w];
+            b += w < warp ? v : 0;
+            tt += v;
+        }
+        pos[k] = b + incl[k] - cnt[k];
+        tot[k] = tt;
     }
-    int32_t p0 = b0 + s0 - c0, p1 = b1 + s1 - c1;
     for (int32_t i = i0; i < i1; ++i) {
-        if (((sub_ptr[i + 1] - sub_ptr[i] + 15) & ~15) <= small) work[n_sub + p1++] = i;
-        else work[p0++] = i;
+        const int k = size_class(sub_ptr[i + 1] - sub_ptr[i], small);
+        work[(int64_t)k * n_sub + pos[k]++] = i;
     }
-    if (t == 0) {
-        work_n[0] = t0;
-        work_n[1] = t1;
-    }
+    if (t == 0)
+        for (int k = 0; k < 3; ++k) work_n[k] = tot[k];
 }
 
 __global__ void k_d1_fixup(int64_t nnz, double mu1, const double* d1mu, double* d1) {
@@ -461,11 +465,14 @@ __global__ void __launch_bounds__(FP64_THREADS) k_fermi_fp64(PassArgs a) {
             if (slot == TR_MAXW)
                 for (int r = threadIdx.x; r < n; r += blockDim.x)
                     v = fmax(v, 0.25 * a.beta * (1.0 - Y[(int64_t)r * (n + 1)]));
+            if (slot == TR_MAXWC)
+                for (int64_t e = c0 + threadIdx.x; e < c1; e += blockDim.x)
+                    v = fmax(v, 0.25 * a.beta * (1.0 - Y[(int64_t)a.core_pos[e] * (n + 1)]));
             red[threadIdx.x] = v;
             __syncthreads();
             for (int o = blockDim.x / 2; o > 0; o >>= 1) {
                 if (threadIdx.x < o)
-                    red[threadIdx.x] = slot == TR_MAXW ? fmax(red[threadIdx.x], red[threadIdx.x + o])
+                    red[threadIdx.x] = trace_slot_is_max(slot) ? fmax(red[threadIdx.x], red[threadIdx.x + o])
                                                        : red[threadIdx.x] + red[threadIdx.x + o];
                 __syncthreads();
             }
@@ -504,10 +511,17 @@ struct DensityLayout {
     float* hblk;        // split: (1 + m) * pool_stride dense gathered blocks (FP32)
     double* hdiag;      // split: sub_nnz FP64 diagonals of h^(i)
     double* h1max;      // split: n_sub * m largest |h1| row sums
-    int32_t* work;      // split: subgraph lists of the two size classes (2 x n_sub)
-    int32_t* work_n;    // split: their lengths (2)
+    int32_t* work;      // split: subgraph lists of the three size classes (3 x n_sub)
+    int32_t* work_n;    // split: their lengths (3) and the tiled launch's work counter
+    uint8_t* big;       // split, |S_i| > 128: per-CTA scratch of the tiled kernel
+    int64_t big_stride; // bytes per CTA
+    int32_t big_ctas;   // CTAs the scratch serves
+    int32_t big_npmax;  // round16(max |S_i|)
     int64_t pool_stride;
 };
+
+// CTAs of the tiled kernel: one per SM at most, within a scratch budget
+constexpr int64_t BIG_SCRATCH_BUDGET = (int64_t)24 << 30;
 
 DensityLayout layout_density(Arena& ar, const gb_part* P, int32_t m, int precision) {
     DensityLayout L;
@@ -544,8 +558,21 @@ DensityLayout layout_density(Arena& ar, const gb_part* P, int32_t m, int precisi
         L.hblk = ar.take<float>((1 + m) * L.pool_stride);
         L.hdiag = ar.take<double>(P->sub_nnz);
         L.h1max = ar.take<double>(n_sub * (int64_t)(m > 0 ? m : 1));
-        L.work = ar.take<int32_t>(2 * n_sub);
+        L.work = ar.take<int32_t>(3 * n_sub);
         L.work_n = ar.take<int32_t>(8);
+        L.big = nullptr;
+        L.big_stride = 0;
+        L.big_ctas = 0;
+        L.big_npmax = 0;
+        if (P->max_sub > GB_SPLIT_MAX_N) {
+            L.big_npmax = (P->max_sub + 15) & ~15;
+            L.big_stride = (big_cta_bytes(L.big_npmax, m) + 255) & ~(int64_t)255;
+            int64_t ctas = n_sub < GB_BIG_MAX_CTAS ? n_sub : GB_BIG_MAX_CTAS;
+            const int64_t fit = BIG_SCRATCH_BUDGET / L.big_stride;
+            if (ctas > fit) ctas = fit > 0 ? fit : 1;
+            L.big_ctas = (int32_t)ctas;
+            L.big = ar.take<uint8_t>((size_t)(ctas * L.big_stride));
+        }
     }
     return L;
 }
@@ -608,7 +635,8 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
     if (o.min_steps <= 0) o.min_steps = 6;
     if (o.ns_iters <= 0) o.ns_iters = split ? 2 : 3;
     const double tol_d = o.tol_d > 0.0 ? o.tol_d : (split ? 1e-6 : 1e-11);
-    if (split && P->max_sub > GB_SPLIT_MAX_N) return GB_ERR_UNSUPPORTED;
+    if (split && P->max_sub > GB_BIG_MAX_N) return GB_ERR_UNSUPPORTED;
+    const bool big = split && P->max_sub > GB_SPLIT_MAX_N;
     if (!D->ptr) return GB_ERR_ARG;  // the value positions follow the column pointers
 
     h->launches = 0;
@@ -690,12 +718,23 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
     a.hblk_stride = L.pool_stride;
     a.hdiag = L.hdiag;
     a.h1max = L.h1max;
+    a.big_scratch = L.big;
+    a.big_stride = L.big_stride;
+    a.big_npmax = L.big_npmax;
+    a.big_counter = split ? L.work_n + 3 : nullptr;
     a.err = L.err;
     // spectral bounds.  Split path: the gather of the dense principal
     // submatrices of H and H1 (once per call: they do not depend on mu) also
     // yields the Gershgorin intervals.
+    const bool lists = split && (o.split_small_npad > 0 || big);
+    int big_grid = 0;
+    if (big) {
+        int sms = 0;
+        GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+        big_grid = L.big_ctas < sms ? L.big_ctas : sms;
+    }
     if (split) {
-        if (o.split_small_npad > 0)
+        if (lists)
             GB_LAUNCH(h, k_class_lists, 1, CLASS_THREADS, 0, n_sub, P->sub_ptr, o.split_small_npad, L.work,
                       L.work_n);
         GB_TRY(launch_split_gather(h, a, L.hblk, L.hdiag));
@@ -730,17 +769,24 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
         a.mu = mu;
         GB_CUDA(cudaEventRecord(ev0, st));
         if (split) {
-            // the 128-column configuration (for its size class when the small
-            // one takes subgraphs), then the small one
+            // the 128-column configuration (for its size class when another
+            // class takes subgraphs), the small one, the tiled one
             a.work = L.work;
             a.work_n = L.work_n;
-            if (o.split_small_npad > 0) GB_TRY(launch_split_pass_listed(h, a));
+            if (lists) GB_TRY(launch_split_pass_listed(h, a));
             else GB_TRY(launch_split_pass(h, a));
             if (o.split_small_npad > 0) {
                 PassArgs b = a;
                 b.work = L.work + n_sub;
                 b.work_n = L.work_n + 1;
                 GB_TRY(launch_split_pass_small(h, b));
+            }
+            if (big) {
+                PassArgs b = a;
+                b.work = L.work + 2 * (int64_t)n_sub;
+                b.work_n = L.work_n + 2;
+                GB_CUDA(cudaMemsetAsync(b.big_counter, 0, sizeof(int32_t), st));
+                GB_TRY(launch_split_pass_big(h, b, big_grid));
             }
         } else {
             GB_LAUNCH(h, k_fermi_fp64, sub_grid, FP64_THREADS, 0, a);
@@ -761,9 +807,10 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
         const double dn = a.beta * sums[TR_DD];
         // Converged when the occupation residual is within tol_occ * N_occ, or
         // when the remaining Newton correction |resid / dn| would move every
-        // element of D by less than tol_dmu (|dD_jk| <= |dmu| max diag d1_mu).
+        // collected element of D by less than tol_d (first order, |dD_jk| <=
+        // |dmu| sqrt(d1_mu_jj d1_mu_kk) with k a core vertex: d1_mu is PSD).
         const double dmu_newton = dn > 0.0 ? fabs(resid) / dn : INFINITY;
-        const double d_bound = dmu_newton * sums[TR_MAXW];
+        const double d_bound = dmu_newton * sqrt(fmax(sums[TR_MAXW], 0.0) * fmax(sums[TR_MAXWC], 0.0));
         // Noise floor: once a Newton step no longer halves the residual, the
         // trace round-off dominates and further passes only move mu within it;
         // that floor is accepted when its D-change bound is small.

@@ -7,18 +7,26 @@
 #include "common.cuh"
 
 constexpr int GB_MAX_RHS = 8;
-constexpr int GB_SPLIT_MAX_N = 128;  // largest subgraph of the tensor-core kernel
+constexpr int GB_SPLIT_MAX_N = 128;  // largest subgraph of the one-tile tensor-core kernels
+constexpr int GB_BIG_MAX_N = 2048;   // largest subgraph of the tiled tensor-core kernel
+// per-CTA scratch of the tiled kernel: staged images (hi/lo parts) and FP32
+// matrices of the subgraph in flight, sized by the largest subgraph
+constexpr int GB_BIG_IMAGES_FIXED = 16;  // + 2 per right-hand side
+constexpr int GB_BIG_F32 = 4;
+constexpr int GB_BIG_MAX_CTAS = 160;
 // sizes the response scratch of the persistent tensor-core kernels: 64 KB per
 // RHS for each of up to this many 128-column CTAs (a small-configuration CTA
 // takes 32 KB, so twice as many of those fit)
 constexpr int GB_SPLIT_MAX_CTAS = 256;
 
 // Per-subgraph trace slots (tr[i * tr_stride + k])
-// TR_MAXW is reduced with max (the largest diagonal element of d1_mu over all
-// rows of all subgraphs, which bounds every element of the PSD d1_mu); the
-// other slots are summed.
-enum TraceSlot { TR_D = 0, TR_DD = 1, TR_D1MU = 2, TR_FLOPS = 3, TR_MAXW = 4, TR_D1LAM = 5 };
-constexpr int TR_FIXED = 5;  // slots before the per-RHS d1_lambda traces
+// TR_MAXW and TR_MAXWC are reduced with max: the largest diagonal element of
+// d1_mu over all rows, and over the core rows, of all subgraphs.  A collected
+// element (j in S_i, k in core_i) of the PSD d1_mu is bounded by
+// sqrt(d1_mu_jj d1_mu_kk) <= sqrt(MAXW MAXWC).  The other slots are summed.
+enum TraceSlot { TR_D = 0, TR_DD = 1, TR_D1MU = 2, TR_FLOPS = 3, TR_MAXW = 4, TR_MAXWC = 5, TR_D1LAM = 6 };
+constexpr int TR_FIXED = 6;  // slots before the per-RHS d1_lambda traces
+__host__ __device__ __forceinline__ bool trace_slot_is_max(int k) { return k == TR_MAXW || k == TR_MAXWC; }
 
 // Matrix products one pass performs on a subgraph with s steps, J Newton-
 // Schulz corrections and m right-hand sides: Taylor start 3 + 6m, every step
@@ -80,8 +88,27 @@ struct PassArgs {
     const double* hdiag;
     // split path: largest row sum of |h1_r^(i)|, at h1max[i * m + r]
     double* h1max;
+    // tiled split path (|S_i| > 128): per-CTA scratch (big_stride bytes each,
+    // laid out for subgraphs of up to big_npmax = round16(max |S_i|) orbitals)
+    // and the dynamic work counter of the launch (zeroed before it)
+    uint8_t* big_scratch;
+    int64_t big_stride;
+    int32_t big_npmax;
+    int32_t* big_counter;
     int* err;
 };
+
+// bytes of one CTA's scratch of the tiled kernel for subgraphs of up to
+// npmax (a multiple of 16) orbitals and m right-hand sides: staged images
+// (hi and lo parts of 128 nrb x npmax 16-bit values each), FP32 matrices
+// (128 nrb x npmax), the per-core trace terms
+__host__ __device__ __forceinline__ int64_t big_cta_bytes(int npmax, int m) {
+    const int64_t nrb = (npmax + 127) / 128;
+    const int64_t img = 2 * 128 * nrb * npmax * 2;
+    const int64_t f32 = 128 * nrb * npmax * 4;
+    const int64_t tv = (int64_t)(3 + GB_MAX_RHS) * npmax * 4;
+    return (GB_BIG_IMAGES_FIXED + 2 * m) * img + GB_BIG_F32 * f32 + ((tv + 255) & ~(int64_t)255);
+}
 
 // Step count s so that x0 = beta (h - mu) / 2^(s+1) has spectral radius <= 1:
 // 2^s >= beta max|eps - mu| / 2, bounded below by min_steps.
@@ -98,3 +125,6 @@ int launch_split_pass(gb_handle* h, const PassArgs& a);
 int launch_split_pass_listed(gb_handle* h, const PassArgs& a);
 int launch_split_pass_small(gb_handle* h, const PassArgs& a);
 int launch_split_gather(gb_handle* h, const PassArgs& a, float* hblk, double* hdiag);
+// the tiled configuration for round16(|S_i|) > 128 over its list (a.work),
+// one subgraph per CTA at a time, dynamically scheduled; grid CTAs
+int launch_split_pass_big(gb_handle* h, const PassArgs& a, int grid);

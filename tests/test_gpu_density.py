@@ -158,7 +158,7 @@ def test_ragged_random_subgraphs(gb, precision):
 
 def test_fp64_paths_of_two_large_subgraphs(gb):
     # graph squared (paths of length two): subgraphs of 256-313 orbitals on the
-    # FP64 path; the split path refuses them (above its 128-row tile)
+    # FP64 path
     wl, system, h1 = make_workload("water64", n_rhs=1)
     H = system.H
     adj = o_graph(H.n, H.indptr, H.indices, H.data, wl.tau, paths2=True)
@@ -174,9 +174,6 @@ def test_fp64_paths_of_two_large_subgraphs(gb):
     # determined); Tr D1 = 0 keeps the count under the perturbation
     assert abs(R.report["occ_residual"]) <= 1e-10 * system.n_occ
     assert abs(np.trace(dense_result(R.D, R.D1[0].val))) < 1e-9
-    bad = gb.density_and_response(Hd, [to_device(h1[0])], wl.kT, system.n_electrons, P, precision="fp16x3",
-                                  raise_on_error=False)
-    assert bad.status == 8  # GB_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp16x3"])
@@ -262,12 +259,14 @@ def test_error_statuses(gb):
     with pytest.raises(gb.GbError) as e:
         gb.density_and_response(bad, H1d, kT, system.n_electrons, P)
     assert e.value.status == 6  # GB_ERR_NAN
-    # split precision refuses subgraphs above 128 orbitals
-    Hc, _ = _random_system(200, 3, density=0.2)
+    # split precision refuses subgraphs above 2,048 orbitals (the tiled
+    # kernel's limit); the FP64 path has none
+    Hc, _ = _random_system(2100, 3, density=0.002)
     G = gb.graph_build(to_device(Hc), 0.0)
-    Pb = gb.partition(G, torch.zeros(200, dtype=torch.int32))
+    Pb = gb.partition(G, torch.zeros(2100, dtype=torch.int32))
+    assert Pb.max_sub == 2100
     with pytest.raises(gb.GbError) as e:
-        gb.density_and_response(to_device(Hc), [], 0.2, 200.0, Pb, precision="fp16x3")
+        gb.density_and_response(to_device(Hc), [], 0.2, 2000.0, Pb, precision="fp16x3")
     assert e.value.status == 8  # GB_ERR_UNSUPPORTED
     # a pass limit of one from a far start reports non-convergence with outputs
     R = gb.density_and_response(Hd, H1d, kT, system.n_electrons, P, mu0=-20.0, max_newton=1,
@@ -345,3 +344,111 @@ def test_plan_autotune(gb):
     assert eD <= TOL["fp16x3"] and eD1 <= TOL["fp16x3"]
     with pytest.raises(ValueError):
         gb.plan_autotune(Hd, H1d, kT, ne, P, ref.mu, precision="fp64", handle=h)
+
+
+# ---- subgraphs above 128 orbitals: the tiled split-precision kernel --------
+
+@pytest.mark.parametrize("precision", ["fp16x3", "bf16x3"])
+def test_split_paths_of_two_water64(gb, precision):
+    # paths-of-two graph of the 64-water box: every subgraph holds 256-313
+    # orbitals (3 row blocks, 2-3 column tiles, ragged last K chunk)
+    wl, system, h1 = make_workload("water64", n_rhs=2)
+    H = system.H
+    adj = o_graph(H.n, H.indptr, H.indices, H.data, wl.tau, paths2=True)
+    part = o_part(adj, system.orb_group)
+    assert part.sizes().min() > 128
+    ref = oracle_graph(H, h1, wl.kT, system.n_occ, part)
+    Hd = to_device(H)
+    P = gb.partition(gb.graph_build(Hd, wl.tau, paths2=True), torch.as_tensor(system.orb_group))
+    R = gb.density_and_response(Hd, [to_device(h) for h in h1], wl.kT, system.n_electrons, P,
+                                precision=precision, mu0=ref.mu + 0.05)
+    eD, eD1 = max_abs_block_error(R, ref, part)
+    print(f"paths2 water64 {precision}: sizes {part.sizes().min()}..{part.sizes().max()} max|dD|={eD:.2e} "
+          f"max|dD1|={eD1:.2e} dmu={R.mu - ref.mu:.2e} passes={R.report['passes']}")
+    assert eD <= TOL[precision] and eD1 <= TOL[precision]
+    assert abs(R.report["occ_residual"]) <= 1e-6 * system.n_occ
+    # at the oracle's mu: the arithmetic of the tiled recursion alone
+    Rf = gb.density_and_response(Hd, [to_device(h) for h in h1], wl.kT, system.n_electrons, P,
+                                 precision=precision, mu0=ref.mu, max_newton=1, raise_on_error=False)
+    eD, eD1 = max_abs_block_error(Rf, ref, part)
+    assert eD <= TOL[precision] and eD1 <= TOL[precision]
+
+
+def test_split_chains_uncapped(gb):
+    # the heterogeneous chain system with its ~30-atom coordinate-bisection
+    # cores as they come (subgraphs of 227-367 orbitals), no size cap
+    wl, system, h1 = make_workload("chains_small", n_rhs=1)
+    H = system.H
+    adj = o_graph(H.n, H.indptr, H.indices, H.data, wl.tau)
+    part = o_part(adj, system.orb_group)
+    assert part.sizes().max() > 128
+    ref = oracle_graph(H, h1, wl.kT, system.n_occ, part, workers=4)
+    Hd = to_device(H)
+    P = gb.partition(gb.graph_build(Hd, wl.tau), torch.as_tensor(system.orb_group))
+    R = gb.density_and_response(Hd, [to_device(h1[0])], wl.kT, system.n_electrons, P, precision="fp16x3")
+    eD, eD1 = max_abs_block_error(R, ref, part)
+    print(f"chains uncapped: sizes {part.sizes().min()}..{part.sizes().max()} max|dD|={eD:.2e} "
+          f"max|dD1|={eD1:.2e} dmu={R.mu - ref.mu:.2e}")
+    assert eD <= TOL["fp16x3"] and eD1 <= TOL["fp16x3"]
+
+
+@pytest.mark.parametrize("small", [0, 32])
+def test_split_three_size_classes(gb, small):
+    # uneven subgraphs from 1 to ~600 orbitals in one call: the small
+    # configuration, the 128-column one and the tiled one side by side
+    Hc, H1c = _random_system(1500, 21, density=0.004)
+    n = Hc.n
+    rng = np.random.default_rng(22)
+    block = rng.integers(1, 60, size=n)
+    groups = np.repeat(np.arange(n), block)[:n].astype(np.int32)
+    groups = np.unique(groups, return_inverse=True)[1].astype(np.int32)
+    adj = o_graph(n, Hc.indptr, Hc.indices, Hc.data, 0.0)
+    part = o_part(adj, groups)
+    npads = (part.sizes() + 15) // 16 * 16
+    assert (npads > 128).any() and (npads <= 128).any()
+    kT, ne = 0.3, 2 * 600.0
+    ref = oracle_graph(Hc, [H1c], kT, ne / 2, part, workers=4)
+    Hd, H1d = to_device(Hc), [to_device(H1c)]
+    P = gb.partition(gb.graph_build(Hd, 0.0), torch.as_tensor(groups))
+    R = gb.density_and_response(Hd, H1d, kT, ne, P, precision="fp16x3", mu0=ref.mu + 0.1,
+                                split_small_npad=small)
+    eD, eD1 = max_abs_block_error(R, ref, part)
+    print(f"three classes (small<={small}): sizes {part.sizes().min()}..{part.sizes().max()}, "
+          f"{(npads > 128).sum()} tiled; max|dD|={eD:.2e} max|dD1|={eD1:.2e} dmu={R.mu - ref.mu:.2e}")
+    assert eD <= TOL["fp16x3"] and eD1 <= TOL["fp16x3"]
+
+
+def test_split_single_large_subgraph_equals_full(gb):
+    # one core holding all 300 orbitals: the tiled kernel's result is the full
+    # Fermi function and response of H (Eq. Fermi without a graph)
+    Hc, H1c = _random_system(300, 12, density=0.05)
+    n = Hc.n
+    Hd = to_device(Hc)
+    P = gb.partition(gb.graph_build(Hd, 0.0), torch.zeros(n, dtype=torch.int32))
+    assert P.n_sub == 1 and P.max_sub == n
+    from oracle import oracle_full
+    full = oracle_full(Hc.to_dense(), [H1c.to_dense()], 0.25, 120.0)
+    R = gb.density_and_response(Hd, [to_device(H1c)], 0.25, 240.0, P, precision="fp16x3", mu0=full.mu)
+    eD = np.abs(dense_result(R.D) - full.D).max()
+    eD1 = np.abs(dense_result(R.D, R.D1[0].val) - full.D1[0]).max()
+    print(f"single 300-orbital subgraph: max|dD|={eD:.2e} max|dD1|={eD1:.2e}")
+    assert eD <= TOL["fp16x3"] and eD1 <= TOL["fp16x3"]
+
+
+def test_split_paths_of_two_water1k(gb):
+    # the 1,000-water box on its paths-of-two graph (subgraphs of 292-413
+    # orbitals, one per molecule): 1,000 tiled subgraphs in one launch
+    wl, system, h1 = make_workload("water1k", n_rhs=1)
+    H = system.H
+    adj = o_graph(H.n, H.indptr, H.indices, H.data, wl.tau, paths2=True)
+    part = o_part(adj, system.orb_group)
+    ref = oracle_graph(H, h1, wl.kT, system.n_occ, part, workers=8)
+    Hd = to_device(H)
+    P = gb.partition(gb.graph_build(Hd, wl.tau, paths2=True), torch.as_tensor(system.orb_group))
+    R = gb.density_and_response(Hd, [to_device(h1[0])], wl.kT, system.n_electrons, P, precision="fp16x3",
+                                mu0=ref.mu - 0.02)
+    eD, eD1 = max_abs_block_error(R, ref, part)
+    print(f"paths2 water1k: sizes {part.sizes().min()}..{part.sizes().max()} max|dD|={eD:.2e} "
+          f"max|dD1|={eD1:.2e} dmu={R.mu - ref.mu:.2e} passes={R.report['passes']} "
+          f"pass_ms={R.report['pass_kernel_ms'] / R.report['passes']:.1f}")
+    assert eD <= TOL["fp16x3"] and eD1 <= TOL["fp16x3"]
