@@ -37,33 +37,31 @@ METRIC = "orbitals/s for D+D1 on 60k-orbital box, mixed vs FP64 path, max|Î”D|â‰
 WORKLOAD = "water10k"
 CONFIG_TEXT = ("10,000 H2O (60,000 orbitals), periodic box 66.9 A, sp tight binding, kT 0.2 eV, "
                "two-pass graph |H| > 1e-4 or |D_1| > 1e-4 (D_1 from a first solve on the H graph), one "
-               "molecule per core (cores over 128 orbitals split into atoms), one H1")
-SUB_CAP = 128  # largest subgraph of the tensor-core kernel
+               "molecule per core, one H1")
+COMPANIONS = "water10k_kT0.05,water10k_kT0.05_tau1e-4,water10k_tau1e-6"
+
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_fermi_split_traffic_water10k.json")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2212_01997_gb300", "csrc", f) for f in ("mixed.cu", "tc.cuh")]
 
 
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_fermi_split_traffic_water10k.md")
-KERNEL_SOURCE = os.path.join(ROOT, "paper_2212_01997_gb300", "csrc", "mixed.cu")
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
 
 
 def recorded_traffic():
-    """DRAM bytes per k_fermi_split launch from the recorded ncu capture of the
-    headline workload, or None when the kernel source changed since."""
-    import hashlib
+    """DRAM bytes per launch of the one-tile recursion kernel from the ncu
+    capture recorded in profiles/ (JSON), or None when its sources changed
+    since (the record carries their hash)."""
     try:
-        text = open(TRAFFIC_FILE).read()
-        src = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
-    except OSError:
-        return None
-    fields = {}
-    for ln in text.splitlines():
-        if ":" in ln and ln.strip().startswith(("traffic_bytes_per_launch", "kernel_source_sha256")):
-            k, v = ln.split(":", 1)
-            fields[k.strip()] = v.strip().strip("`")
-    if fields.get("kernel_source_sha256") != src:
-        return None
-    try:
-        return float(fields["traffic_bytes_per_launch"])
-    except (KeyError, ValueError):
+        rec = json.load(open(TRAFFIC_FILE))
+        if rec.get("kernel_source_sha256") != kernel_source_hash():
+            return None
+        return float(rec["traffic_bytes_per_launch"])
+    except (OSError, ValueError, KeyError, TypeError):
         return None
 
 
@@ -110,14 +108,17 @@ def parse():
     p.add_argument("--impl", default="gbqr", choices=["gbqr", "reference"])
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--fp64-steps", type=int, default=2)
-    p.add_argument("--companion", default="water10k_kT0.05")
+    p.add_argument("--companion", default=COMPANIONS,
+                   help="comma-separated workloads timed beside the headline (empty: none)")
+    p.add_argument("--moving", type=int, default=4,
+                   help="trajectory geometries of the headline box timed with changing inputs (0: none)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--split-small", type=int, default=-1,
                    help="npad bound of the small split configuration (-1: autotuned per workload)")
     p.add_argument("--trajectory", action="store_true",
                    help="the rank-m workload instead: m=6 responses along a thermal trajectory of "
                         "20,000 waters (steps/s, p50/p99 step latency)")
-    p.add_argument("--geometries", type=int, default=8, help="distinct trajectory geometries (cycled)")
+    p.add_argument("--geometries", type=int, default=100, help="distinct trajectory geometries")
     return p.parse_args()
 
 
@@ -137,7 +138,6 @@ def cpu_baseline(workload_name: str, budget_s: float = 15.0):
     budget_s seconds have passed.
     """
     from oracle import graph_build as o_graph, oracle_graph, partition as o_part
-    from oracle.graph import partition_capped as o_part_capped
     from synth import WORKLOADS, make_workload
     from synth.workloads import Workload
 
@@ -152,14 +152,14 @@ def cpu_baseline(workload_name: str, budget_s: float = 15.0):
     reps = 0
     while True:
         adj = o_graph(H.n, H.indptr, H.indices, H.data, wl.tau, d_prev=d_1)
-        part = o_part_capped(adj, system.orb_group, system.orb_atom, SUB_CAP)
+        part = o_part(adj, system.orb_group)
         oracle_graph(H, h1, wl.kT, system.n_occ, part, workers=workers)
         reps += 1
         el = time.perf_counter() - t0
         if el > budget_s or reps >= 50:
             break
     return {"value": reps * H.n / el, "unit": "orbitals/s", "cores": workers, "kind": "oracle",
-            "sample": f"{reps} x oracle second-pass step (graph from H and D_1, capped partition, eigh "
+            "sample": f"{reps} x oracle second-pass step (graph from H and D_1, one molecule per core, eigh "
                       f"per subgraph, mu, mu1, collect) of the 1,000-water box ({H.n} orbitals, kT {wl.kT}, "
                       f"tau {wl.tau}, m=1), process pool of {workers}", "seconds": el}
 
@@ -222,7 +222,34 @@ class ClockSampler:
 SPLIT_SMALL = {"npad": 0, "auto": False}
 
 
-def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world, dist, e2e_steps=0):
+def atom_map(orb_atom):
+    """The orbitals of each atom as CSR (atom_ptr, atom_orb), for the charges."""
+    import numpy as np
+    import torch
+    order = np.argsort(orb_atom, kind="stable").astype(np.int32)
+    ptr = np.concatenate([[0], np.cumsum(np.bincount(orb_atom))]).astype(np.int64)
+    return torch.as_tensor(ptr), torch.as_tensor(order)
+
+
+def moving_geometries(workload, count):
+    """H and H1 of the workload's box at the first `count` steps of its thermal
+    trajectory (Maxwell 300 K, dt 0.25 fs, no forces): inputs that change
+    between timed steps."""
+    import dataclasses as dc
+
+    from synth import make_workload
+    from synth.water import tb_hamiltonian, thermal_trajectory, water_perturbation
+    wl, system, _ = make_workload(workload, n_rhs=0)
+    out = []
+    for k, pos in enumerate(thermal_trajectory(system, count, seed=20221204 + 1000)):
+        H, _ = tb_hamiltonian(pos, system.species, system.box)
+        moved = dc.replace(system, positions=pos, H=H)
+        out.append((H, [water_perturbation(moved, 20221204 + 1000 * (k + 1))]))
+    return out
+
+
+def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world, dist, e2e_steps=0,
+            moving=0):
     """Time the whole hot path on one workload; return the measurements."""
     import numpy as np
     import torch
@@ -233,17 +260,17 @@ def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world,
     H = gb.DeviceCSR.from_arrays(system.H.n, system.H.indptr, system.H.indices, system.H.data, dev)
     H1 = [gb.DeviceCSR.from_arrays(h.n, h.indptr, h.indices, h.data, dev) for h in h1]
     groups = torch.as_tensor(system.orb_group, device=dev)
-    atoms = torch.as_tensor(system.orb_atom, device=dev)
     n_groups = int(system.orb_group.max()) + 1
-    n_atoms = int(system.orb_atom.max()) + 1
+    aptr, aorb = atom_map(system.orb_atom)
+    aptr, aorb = aptr.to(dev), aorb.to(dev)
+    zval = torch.as_tensor(system.z_valence, device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     launches = {"n": 0}
 
     def step(precision, mu0, d_prev, Hs=H, H1s=H1, max_newton=0):
         G = gb.graph_build(Hs, wl.tau, d_prev=d_prev, handle=handle)
         launches["n"] += handle.lib.gb_launch_count(handle.h)
-        P = gb.partition(G, groups, n_groups, subgroups=atoms, n_subgroups=n_atoms, max_sub=SUB_CAP,
-                         handle=handle)
+        P = gb.partition(G, groups, n_groups, handle=handle)
         launches["n"] += handle.lib.gb_launch_count(handle.h)
         R = gb.density_and_response(Hs, H1s, wl.kT, system.n_electrons, P, precision=precision, mu0=mu0,
                                     handle=handle, max_newton=max_newton, raise_on_error=max_newton == 0,
@@ -251,16 +278,14 @@ def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world,
         launches["n"] += R.report["kernel_launches"]
         return P, R
 
-    def timed(precision, k, w, mu0, d_prev, adaptive=False):
-        """w untimed then k timed steps; the graph follows the previous D when adaptive."""
+    def timed(precision, k, w, mu0, d_prev):
+        """w untimed then k timed steps on the same inputs (warm-started mu)."""
+        P = R = None
         for _ in range(w):
             P, R = step(precision, mu0, d_prev)
             mu0 = R.mu
-            if adaptive:
-                d_prev = R.D
-        times, kms, passes, flops = [], [], [], []
+        times, kms, passes, flops, flops_s = [], [], [], [], []
         launches["n"] = 0
-        last_input = d_prev
         for _ in range(k):
             flush.zero_()
             torch.cuda.synchronize(dev)
@@ -274,40 +299,43 @@ def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world,
             kms.append(R.report["pass_kernel_ms"])
             passes.append(R.report["passes"])
             flops.append(R.report["gemm_flops"])
+            flops_s.append(R.report["gemm_flops_per_step_count"])
             mu0 = R.mu
-            last_input = d_prev
-            if adaptive:
-                d_prev = R.D
-        return P, R, times, kms, passes, flops, launches["n"], last_input
+        return P, R, times, kms, passes, flops, flops_s, launches["n"]
+
+    def charges(R):
+        return gb.mulliken_charges(R.D, R.D1, aptr, aorb, zval, handle=handle)
 
     out = {"workload": workload, "wl": wl, "system": system}
     # split precision (FP16 parts): the first pass, a cold start on the H
     # graph, gives D_1; then warm-started second-pass steps on the graph of
     # H and D_1 (rebuilt every step)
-    _, R1, _, _, _, _, _, _ = timed("fp16x3", 0, 1, math.nan, None)
+    _, R1, *_ = timed("fp16x3", 0, 1, math.nan, None)
     d_1 = R1.D
-    _, R0, _, _, _, _, _, _ = timed("fp16x3", 0, max(warmup, 3), R1.mu, d_1)
+    _, R0, *_ = timed("fp16x3", 0, max(warmup, 3), R1.mu, d_1)
     if SPLIT_SMALL["auto"]:
         # size bins -> configuration (gb_plan_autotune), outside the timed region
         Gp = gb.graph_build(H, wl.tau, d_prev=d_1, handle=handle)
-        Pp = gb.partition(Gp, groups, n_groups, subgroups=atoms, n_subgroups=n_atoms, max_sub=SUB_CAP,
-                          handle=handle)
+        Pp = gb.partition(Gp, groups, n_groups, handle=handle)
         plan = gb.plan_autotune(H, H1, wl.kT, system.n_electrons, Pp, R0.mu, handle=handle)
         SPLIT_SMALL["npad"] = plan["split_small_npad"]
         out["split_plan"] = plan
-        _, R0, _, _, _, _, _, _ = timed("fp16x3", 0, 1, R0.mu, d_1)
+        _, R0, *_ = timed("fp16x3", 0, 1, R0.mu, d_1)
     out["split_small_npad"] = SPLIT_SMALL["npad"]
     clocks = ClockSampler(dev.index or 0)
     clocks.start()
-    P, Rm, t_m, k_m, pass_m, fl_m, n_launch, dp = timed("fp16x3", steps, 0, R0.mu, d_1)
+    P, Rm, t_m, k_m, pass_m, fl_m, fls_m, n_launch = timed("fp16x3", steps, 0, R0.mu, d_1)
     out["clocks"] = clocks.stop()
     t_step = max_over_ranks(statistics.mean(t_m), world, dist, dev)
     sizes = (P.sub_ptr[1:] - P.sub_ptr[:-1]).float()
     out.update(P=P, ms=t_step, value=whole_job_rate(system.n_orb, t_step, world), launches=n_launch,
                passes=pass_m[-1], max_steps=Rm.report["max_steps"], mu=Rm.mu, mu1=Rm.mu1[0],
                kernel_ms=statistics.mean(k / p for k, p in zip(k_m, pass_m)),
-               flops=statistics.mean(fl_m), mean_sub=float(sizes.mean().item()))
+               flops=statistics.mean(fl_m), flops_per_step_count=statistics.mean(fls_m),
+               mean_sub=float(sizes.mean().item()), n_tiled=int((sizes > 128).sum().item()))
     Dm, D1m = Rm.D.val.clone(), Rm.D1[0].val.clone()
+    qm, q1m = charges(Rm)
+    qm, q1m = qm.clone(), q1m[0].clone()
     try:  # diagnostic, outside the timed region
         out["max_abs_D_minus_DT"] = csc_asymmetry(system.n_orb, Rm.D.ptr.cpu().numpy(), Rm.D.idx.cpu().numpy(),
                                                   Dm.cpu().numpy())
@@ -315,7 +343,8 @@ def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world,
         out["max_abs_D_minus_DT"] = None
 
     if e2e_steps:
-        # public API from pinned host buffers: H2D of H, H1 and D2H of D, D1
+        # public API from pinned host buffers: H2D of H, H1 and D2H of the
+        # collected D (column pointers, row indices, values) and D1 values
         # inside the region (D_1, the first pass's result, stays on the GPU)
         hp = [torch.as_tensor(a).pin_memory() for a in (system.H.indptr, system.H.indices.astype(np.int32),
                                                         system.H.data)]
@@ -323,7 +352,15 @@ def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world,
                                                          h1[0].data)]
         bi = sum(t.numel() * t.element_size() for t in hp + h1p)
         cap = int(P.out_nnz * 1.25) + 4096
-        host_out = [torch.empty(cap, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+        n1 = system.n_orb + 1
+
+        def host_buffers(cap):
+            return (torch.empty(n1, dtype=torch.int64, pin_memory=True),
+                    torch.empty(cap, dtype=torch.int32, pin_memory=True),
+                    torch.empty(cap, dtype=torch.float64, pin_memory=True),
+                    torch.empty(cap, dtype=torch.float64, pin_memory=True))
+
+        host_out = host_buffers(cap)
         ts_e2e, mu_e, bo = [], Rm.mu, 0
         for it in range(e2e_steps + 1):
             flush.zero_()
@@ -334,27 +371,62 @@ def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world,
             Hd = gb.DeviceCSR(system.n_orb, *[t.to(dev, non_blocking=True) for t in hp])
             H1d = [gb.DeviceCSR(system.n_orb, *[t.to(dev, non_blocking=True) for t in h1p])]
             Pe, Re = step("fp16x3", mu_e, d_1, Hs=Hd, H1s=H1d)
-            if Pe.out_nnz > cap:  # the graph grew past the buffers: grow them, drop this sample
+            it_valid = Pe.out_nnz <= cap
+            if not it_valid:  # the graph grew past the buffers: grow them, drop this sample
                 cap = int(Pe.out_nnz * 1.25) + 4096
-                host_out = [torch.empty(cap, dtype=torch.float64, pin_memory=True) for _ in range(2)]
-                it_valid = False
-            else:
-                it_valid = True
-            host_out[0][: Pe.out_nnz].copy_(Re.D.val, non_blocking=True)
-            host_out[1][: Pe.out_nnz].copy_(Re.D1[0].val, non_blocking=True)
+                host_out = host_buffers(cap)
+            nz = Pe.out_nnz
+            host_out[0].copy_(Re.D.ptr, non_blocking=True)
+            host_out[1][:nz].copy_(Re.D.idx, non_blocking=True)
+            host_out[2][:nz].copy_(Re.D.val, non_blocking=True)
+            host_out[3][:nz].copy_(Re.D1[0].val, non_blocking=True)
             e1.record(stream)
             torch.cuda.synchronize(dev)
-            mu_e, bo = Re.mu, 2 * Pe.out_nnz * 8
+            mu_e, bo = Re.mu, n1 * 8 + nz * (4 + 8 + 8)
             if it > 0 and it_valid:
                 ts_e2e.append(e0.elapsed_time(e1))
         ms_e2e = max_over_ranks(statistics.mean(ts_e2e), world, dist, dev)
         out["e2e"] = {"value": whole_job_rate(system.n_orb, ms_e2e, world), "unit": "orbitals/s",
-                      "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": ms_e2e}
+                      "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": ms_e2e,
+                      "d2h": "collected D (column pointers, row indices, values) and D1 values"}
+
+    if moving:
+        # inputs that change every step: successive geometries of the box's
+        # thermal trajectory, each step's graph estimated from |H| and the
+        # previous step's D (the adaptive estimate along a trajectory), mu
+        # warm-started from the previous step
+        geoms = [(gb.DeviceCSR.from_arrays(Hg.n, Hg.indptr, Hg.indices, Hg.data, dev),
+                  [gb.DeviceCSR.from_arrays(h.n, h.indptr, h.indices, h.data, dev) for h in h1g])
+                 for Hg, h1g in moving_geometries(workload, moving)]
+        mu_v, d_prev = Rm.mu, Rm.D
+        ms_v, passes_v, nnz_v = [], [], []
+        for Hg, H1g in geoms:
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            rank_barrier(world, dist)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            Pv, Rv = step("fp16x3", mu_v, d_prev, Hs=Hg, H1s=H1g)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms_v.append(e0.elapsed_time(e1))
+            passes_v.append(Rv.report["passes"])
+            nnz_v.append(Pv.sub_nnz)
+            mu_v, d_prev = Rv.mu, Rv.D
+        out["moving"] = {"ms_per_step": statistics.mean(ms_v), "passes": passes_v, "steps": len(ms_v),
+                         "value": whole_job_rate(system.n_orb, max_over_ranks(statistics.mean(ms_v), world, dist,
+                                                                              dev), world),
+                         "sum_subgraph_sizes": nnz_v,
+                         "inputs": f"the next {moving} geometries of the box's thermal trajectory (Maxwell 300 "
+                                   "K, dt 0.25 fs; the headline geometry is step 0), one per step; graph from |H| "
+                                   "and the previous step's D"}
 
     # the plain FP64 GPU path on the same graph and partition (same D_1), its
-    # own mu; then both paths at the FP64 mu
-    _, R64, t64, k64, pass64, _, _, _ = timed("fp64", fp64_steps, 1, Rm.mu, dp)
+    # own mu; then the split path at the FP64 mu
+    dp = d_1
+    _, R64, t64, k64, pass64, *_ = timed("fp64", fp64_steps, 1, Rm.mu, dp)
     t64_ms = max_over_ranks(statistics.mean(t64), world, dist, dev)
+    q64, q164 = charges(R64)
     out["fp64"] = {"value": whole_job_rate(system.n_orb, t64_ms, world) / world, "unit": "orbitals/s",
                    "ms_per_step": t64_ms, "passes": pass64[-1], "kernel_ms": statistics.mean(k64),
                    "mu": R64.mu}
@@ -362,6 +434,8 @@ def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world,
     out["accuracy_vs_fp64_gpu"] = {
         "max_abs_dD": float((Dm - R64.D.val).abs().max().item()),
         "max_abs_dD1": float((D1m - R64.D1[0].val).abs().max().item()),
+        "max_abs_dq": float((qm - q64).abs().max().item()),
+        "max_abs_dq1": float((q1m - q164[0]).abs().max().item()),
         "dmu": Rm.mu - R64.mu, "dmu1": Rm.mu1[0] - R64.mu1[0],
         "at_fp64_mu": {"max_abs_dD": float((Rs.D.val - R64.D.val).abs().max().item()),
                        "max_abs_dD1": float((Rs.D1[0].val - R64.D1[0].val).abs().max().item())}}
@@ -430,7 +504,8 @@ def run_trajectory(args, rank, world):
         P = gb.partition(gb.graph_build(Hd, wl.tau, handle=handle), groups, handle=handle)
         R = gb.density_and_response(Hd, H1d, wl.kT, system.n_electrons, P, precision=precision, mu0=mu0,
                                     handle=handle)
-        out = [R.D.val.to("cpu", non_blocking=True)] + [d.val.to("cpu", non_blocking=True) for d in R.D1]
+        out = ([R.D.ptr.to("cpu", non_blocking=True), R.D.idx.to("cpu", non_blocking=True),
+                R.D.val.to("cpu", non_blocking=True)] + [d.val.to("cpu", non_blocking=True) for d in R.D1])
         return P, R, out
 
     mu = math.nan
@@ -477,9 +552,11 @@ def run_trajectory(args, rank, world):
             "config": {"workload": f"{name}: 20000 H2O ({system.n_orb} orbitals), box {system.box:.1f} A, kT "
                                    f"{wl.kT} eV, graph |H| > {wl.tau:g}, one molecule per core, m = {m} H1 per "
                                    f"geometry (fresh seeds), {args.geometries} trajectory geometries "
-                                   f"(Maxwell 300 K, dt 0.25 fs, no forces) cycled",
+                                   f"(Maxwell 300 K, dt 0.25 fs, no forces), "
+                                   + ("one per timed step" if args.geometries >= steps else "cycled"),
                        "n_subgraphs": P.n_sub, "max_subgraph": P.max_sub,
-                       "step": "H2D(H, H1) + graph_build + partition + density_and_response + D2H(D, D1)",
+                       "step": "H2D(H, H1) + graph_build + partition + density_and_response + D2H(D with its "
+                               "structure, D1 values)",
                        "l2": "flushed (512 MB write) before every timed step"},
             "h2d_bytes_per_step": statistics.mean(bi), "d2h_bytes_per_step": bo,
             "fp64_path": {"seconds_per_step": s64, "steps_per_s": 1.0 / s64, "passes": R64.report["passes"]},
@@ -518,10 +595,11 @@ def main():
     handle = gb.Handle(stream, dev)
 
     head = measure(gb, args.workload, args.steps, args.warmup, args.fp64_steps, dev, stream, handle, world,
-                   dist, e2e_steps=max(2, args.steps // 2))
-    comp = None
-    if args.companion and args.companion in __import__("synth").WORKLOADS:
-        comp = measure(gb, args.companion, max(2, args.steps // 2), 2, 1, dev, stream, handle, world, dist)
+                   dist, e2e_steps=max(2, args.steps // 2), moving=args.moving)
+    comps = []
+    for name in [c for c in args.companion.split(",") if c]:
+        if name in __import__("synth").WORKLOADS and name != args.workload:
+            comps.append(measure(gb, name, max(2, args.steps // 2), 2, 1, dev, stream, handle, world, dist))
 
     peaks = {}
     try:
@@ -530,14 +608,20 @@ def main():
         pass
     peak = peaks.get("bf16_tflops", 1900.0)
     achieved = head["flops"] / (head["kernel_ms"] / 1e3) / 1e12
-    roof = {"bound": "tensor", "kernel": "k_fermi_split", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak,
+    achieved_s = head["flops_per_step_count"] / (head["kernel_ms"] / 1e3) / 1e12
+    roof = {"bound": "tensor", "kernel": "split recursion pass (k_fermi_split, and k_fermi_split_big beside it "
+                                         "for subgraphs above 128 orbitals)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": recorded_traffic() if args.workload == WORKLOAD else None,
             "peak_source": ("measured bf16 dense burst (MEASURED_PEAKS.json); the fp16 dense rate is the "
                             "same nominal figure" if "bf16_tflops" in peaks else "fallback 1.9 PFLOP/s bf16"),
             "kernel_ms_per_launch": head["kernel_ms"], "algorithmic_flops_per_launch": head["flops"],
-            "flop_count": "2 |S_i|^3 per matrix product of the recursion, summed over subgraphs; the split "
-                          "terms and the padding to 128 rows are not counted"}
+            "flop_count": "2 |S_i|^3 per matrix product the recursion performs (Taylor start 4 + 6m, each step "
+                          "3 + 2J + 4m, J = 2, m = 1), summed over subgraphs; the split terms and the padding "
+                          "to 128 rows are not counted",
+            "per_step_count": {"achieved": achieved_s, "frac": achieved_s / peak,
+                               "algorithmic_flops_per_launch": head["flops_per_step_count"],
+                               "flop_count": "2 |S_i|^3 s ((2 + 2J) + 3m) + 2 |S_i|^2 |core_i| per subgraph"}}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload)
@@ -551,27 +635,28 @@ def main():
             "config": {"workload": f"{args.workload}: {workload_text(wl, system)}",
                        "n_orbitals": system.n_orb, "n_subgraphs": head["P"].n_sub,
                        "max_subgraph": head["P"].max_sub, "mean_subgraph": round(head["mean_sub"], 1),
+                       "subgraphs_above_128": head["n_tiled"],
                        "m": 1, "kT": wl.kT, "tau": wl.tau,
                        "split_small_npad": head["split_small_npad"], "split_plan": head.get("split_plan"),
                        "l2": "flushed (512 MB write) before every timed step",
                        "parallelism": f"replicas x{world} (independent systems, no collective)",
-                       "step": ("graph_build(H, D_1) + capped partition + density_and_response "
-                                "(warm-started mu); D_1 = first-pass density on the H graph")},
+                       "step": ("graph_build(H, D_1) + partition (one molecule per core) + "
+                                "density_and_response (warm-started mu); D_1 = first-pass density on the H "
+                                "graph")},
             "e2e": head.get("e2e"), "gpu_launches": head["launches"], "roofline": roof, "cpu_baseline": cpu,
             "clocks": head["clocks"], "fp64_path": head["fp64"],
             "mixed_over_fp64": head["value"] / world / head["fp64"]["value"],
             "accuracy_vs_fp64_gpu": head["accuracy_vs_fp64_gpu"],
             "mu": head["mu"], "mu1": head["mu1"], "passes": head["passes"], "max_steps": head["max_steps"],
-            "max_abs_D_minus_DT": head.get("max_abs_D_minus_DT"),
+            "max_abs_D_minus_DT": head.get("max_abs_D_minus_DT"), "moving": head.get("moving"),
         }
-        if comp is not None:
-            cwl, csys = comp["wl"], comp["system"]
-            line["companion"] = {
-                "workload": f"{args.companion}: {workload_text(cwl, csys)}", "value": comp["value"],
-                "unit": "orbitals/s", "ms_per_step": comp["ms"], "fp64_path": comp["fp64"],
-                "mixed_over_fp64": comp["value"] / world / comp["fp64"]["value"],
-                "accuracy_vs_fp64_gpu": comp["accuracy_vs_fp64_gpu"], "clocks": comp["clocks"],
-                "max_steps": comp["max_steps"]}
+        line["companions"] = [{
+            "workload": f"{c['workload']}: {workload_text(c['wl'], c['system'])}", "value": c["value"],
+            "unit": "orbitals/s", "ms_per_step": c["ms"], "fp64_path": c["fp64"],
+            "mixed_over_fp64": c["value"] / world / c["fp64"]["value"], "passes": c["passes"],
+            "accuracy_vs_fp64_gpu": c["accuracy_vs_fp64_gpu"], "clocks": c["clocks"],
+            "max_steps": c["max_steps"], "max_subgraph": c["P"].max_sub, "subgraphs_above_128": c["n_tiled"]}
+            for c in comps]
         print(json.dumps(line))
     if world > 1:
         dist.barrier()
@@ -584,10 +669,9 @@ def workload_text(wl, system):
         return (f"{system.n_atoms} atoms ({system.meta['n_chains']} C/N/O chains of {system.meta['chain_len']} "
                 f"heavy atoms with H caps, {system.meta['n_waters']} H2O; {system.n_orb} orbitals), periodic box "
                 f"{system.box:.1f} A, sp tight binding, kT {wl.kT} eV, {graph}, cores of ~{wl.core_atoms} atoms by "
-                f"coordinate bisection (cores over {SUB_CAP} orbitals split into atoms, then orbitals), one H1")
+                f"coordinate bisection, one H1")
     return (f"{system.meta.get('n_waters')} H2O ({system.n_orb} orbitals), periodic box "
-            f"{system.box:.1f} A, sp tight binding, kT {wl.kT} eV, {graph}, one molecule per core (cores "
-            f"over {SUB_CAP} orbitals split into atoms), one H1")
+            f"{system.box:.1f} A, sp tight binding, kT {wl.kT} eV, {graph}, one molecule per core, one H1")
 
 
 def run_reference(args, rank, world):

@@ -9,6 +9,7 @@
  *   gb_partition             disjoint cores + distance-1 halos       (Fig. 1; Sec. "Choosing the graph partitioning")
  *   gb_density_and_response  D, D1, mu, mu1 on the partitioned graph (Eqs. Fermi, DD0-DD, NewtonRaphson,
  *                                                                      D1, ddlambda, dddmu, dmu_1, dCollect)
+ *   gb_mulliken_charges      atomic charges q, q1 from D, D1       (Sec. "Response in observables")
  *
  * Conventions for every entry point:
  *   - Plain C types only.  Pointers marked [device] are CUDA device pointers,
@@ -143,6 +144,9 @@ typedef struct gb_report {
     double eps_min, eps_max; /* Gershgorin bounds over all subgraphs                      */
     double gemm_flops;       /* algorithmic flops of one pass: 2 |S_i|^3 per matrix product,
                                 summed over the products the recursion performs            */
+    double gemm_flops_per_step_count; /* the same pass counted as 2 |S_i|^3 x s ((2 + 2J)
+                                + 3 m) + 2 |S_i|^2 |core_i| (s steps, J Newton-Schulz
+                                corrections, m right-hand sides)                           */
     double pass_kernel_ms;   /* device time of the recursion kernel, summed over passes
                                 (CUDA events on the handle's stream)                       */
     double mu_d_bound;       /* bound on the change of D the remaining mu step would make
@@ -301,6 +305,32 @@ int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_csr* H1, int
                             double kT, double n_electrons, const gb_part* P,
                             const gb_opts* opts, double* mu_inout, gb_csc* D, gb_csc* D1,
                             double* mu1, gb_report* rep);
+
+/* ---- gb_mulliken_charges ------------------------------------------------ *
+ * Net Mulliken charges of the atoms and their first-order responses from the
+ * collected matrices of gb_density_and_response: the charges are the
+ * subsystem observables the paper forms from D and D1 (Sec. "Response in
+ * observables"; Sec. "Implementation with SCC-DFTB theory", Mulliken charge
+ * vectors).  Orthogonal basis, spin restricted (Tr D = N_occ = Ne / 2):
+ *   q_I    = Z_I - 2 sum_{o in I} D_oo,
+ *   q1_r,I = -2 sum_{o in I} D1_r,oo.
+ *   D        [host] struct of the collected D ([device] ptr, idx, val).
+ *   D1       [host] array of m collected responses (their val arrays are read;
+ *            the structure is D's), m in [0, 8].
+ *   n_atoms  atoms; atom_ptr [device] n_atoms + 1 offsets into atom_orb
+ *            [device], the orbitals of each atom (each in [0, n)).  Each
+ *            atom's sum runs in FP64 over its orbitals in this order, so the
+ *            result is deterministic.
+ *   z_val    [device] valence charge Z_I per atom.
+ *   q        out, [device] n_atoms charges; q1 out, [device] m x n_atoms
+ *            (q1[r * n_atoms + I]); may be NULL when m == 0.
+ * Errors: GB_ERR_ARG (bad sizes, an orbital out of range, a column without
+ * its diagonal), GB_ERR_WORKSPACE (see gb_mulliken_workspace_size).
+ * Synchronises the stream. */
+size_t gb_mulliken_workspace_size(void);
+int gb_mulliken_charges(gb_handle* h, const gb_csc* D, const gb_csc* D1, int32_t m, int32_t n_atoms,
+                        const int64_t* atom_ptr, const int32_t* atom_orb, const double* z_val,
+                        double* q, double* q1);
 
 /* ---- gb_plan_autotune ----------------------------------------------------- *
  * Size bins -> kernel configuration for the split-precision recursion.  The

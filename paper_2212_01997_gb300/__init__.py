@@ -23,7 +23,7 @@ from . import _lib as L
 from ._lib import GbError, PRECISION
 
 __all__ = ["DeviceCSR", "Graph", "Partition", "CSC", "Result", "Handle", "graph_build", "partition",
-           "density_and_response", "plan_autotune", "GbError", "PRECISION", "library"]
+           "density_and_response", "mulliken_charges", "plan_autotune", "GbError", "PRECISION", "library"]
 
 
 def library():
@@ -273,6 +273,32 @@ def density_and_response(H: DeviceCSR, H1: list, kT: float, n_electrons: float, 
         L.check("gb_density_and_response", st)
     report = {k: getattr(rep, k) for k, _ in L.gb_report._fields_}
     return Result(mu.value, [mu1[r] for r in range(m)], D, D1, st, report)
+
+
+def mulliken_charges(D: CSC, D1: list, atom_ptr: torch.Tensor, atom_orb: torch.Tensor, z_val: torch.Tensor, *,
+                     handle: Handle | None = None) -> tuple:
+    """gb_mulliken_charges: q_I = Z_I - 2 sum_o D_oo and q1_r,I = -2 sum_o D1_r,oo.
+
+    ``atom_ptr`` / ``atom_orb``: the orbitals of each atom (CSR); ``z_val``:
+    valence charges.  Returns (q, [q1_r ...]) as device tensors.
+    """
+    hd = handle or _default_handle(D.val.device)
+    lib = hd.lib
+    dev = hd.device
+    m = len(D1)
+    atom_ptr = atom_ptr.to(device=dev, dtype=torch.int64).contiguous()
+    atom_orb = atom_orb.to(device=dev, dtype=torch.int32).contiguous()
+    z_val = z_val.to(device=dev, dtype=torch.float64).contiguous()
+    n_atoms = atom_ptr.numel() - 1
+    hd.workspace(lib.gb_mulliken_workspace_size())
+    q = torch.empty(n_atoms, dtype=torch.float64, device=dev)
+    q1 = torch.empty((max(m, 1), n_atoms), dtype=torch.float64, device=dev)
+    ds = D.struct()
+    d1s = (L.gb_csc * max(m, 1))(*[d.struct(with_index=False) for d in D1])
+    L.check("gb_mulliken_charges", lib.gb_mulliken_charges(hd.h, C.byref(ds), d1s, m, n_atoms, atom_ptr.data_ptr(),
+                                                             atom_orb.data_ptr(), z_val.data_ptr(), q.data_ptr(),
+                                                             q1.data_ptr() if m else None))
+    return q, [q1[r] for r in range(m)]
 
 
 def plan_autotune(H: DeviceCSR, H1: list, kT: float, n_electrons: float, part: Partition, mu: float, *,

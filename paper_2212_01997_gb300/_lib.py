@@ -56,6 +56,7 @@ class gb_report(C.Structure):
                 ("max_sub", C.c_int32), ("mu", C.c_double), ("trace_d", C.c_double),
                 ("dndmu", C.c_double), ("occ_residual", C.c_double), ("trace_d1mu", C.c_double),
                 ("eps_min", C.c_double), ("eps_max", C.c_double), ("gemm_flops", C.c_double),
+                ("gemm_flops_per_step_count", C.c_double),
                 ("pass_kernel_ms", C.c_double), ("mu_d_bound", C.c_double),
                 ("kernel_launches", C.c_int64)]
 
@@ -92,6 +93,9 @@ SIGNATURES = [
                                           C.c_double, C.c_double, C.POINTER(gb_part), C.POINTER(gb_opts),
                                           C.POINTER(C.c_double), C.POINTER(gb_csc), C.POINTER(gb_csc),
                                           C.POINTER(C.c_double), C.POINTER(gb_report)]),
+    ("gb_mulliken_workspace_size", C.c_size_t, []),
+    ("gb_mulliken_charges", C.c_int, [C.c_void_p, C.POINTER(gb_csc), C.POINTER(gb_csc), C.c_int32, C.c_int32,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("gb_plan_autotune", C.c_int, [C.c_void_p, C.POINTER(gb_csr), C.POINTER(gb_csr), C.c_int32, C.c_double,
                                    C.c_double, C.POINTER(gb_part), C.POINTER(gb_opts), C.c_double,
                                    C.POINTER(gb_csc), C.POINTER(gb_csc), C.POINTER(gb_plan)]),

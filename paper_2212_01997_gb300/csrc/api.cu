@@ -16,6 +16,8 @@ extern "C" int gb_create(gb_handle** h, void* stream) {
     p->required_ws = 0;
     p->launches = 0;
     p->ev0 = p->ev1 = nullptr;
+    p->aux = nullptr;
+    p->ev_fork = p->ev_join = nullptr;
     p->plan_valid = 0;
     if (cudaGetDevice(&p->device) != cudaSuccess) {
         delete p;
@@ -29,6 +31,9 @@ extern "C" int gb_destroy(gb_handle* h) {
     if (!h) return GB_ERR_ARG;
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->aux) cudaStreamDestroy(h->aux);
     delete h;
     return GB_OK;
 }

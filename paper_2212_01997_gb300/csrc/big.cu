@@ -889,6 +889,8 @@ __global__ void __launch_bounds__(BT, 1) k_fermi_split_big(PassArgs a) {
                 if (sl == TR_D1MU) v *= a.beta;
             } else if (sl == TR_FLOPS) {
                 v = pass_gemm_flops(K.n, s, a.ns_iters, m);
+            } else if (sl == TR_FLOPS_S) {
+                v = pass_flops_per_step_count(K.n, ncore, s, a.ns_iters, m);
             } else if (sl == TR_MAXWC) {
                 float g = 0.f;
                 for (int e = 0; e < ncore; ++e) g = fmaxf(g, K.tv(T_DD)[e]);
@@ -913,7 +915,7 @@ __global__ void __launch_bounds__(BT, 1) k_fermi_split_big(PassArgs a) {
 
 }  // namespace
 
-int launch_split_pass_big(gb_handle* h, const PassArgs& a, int grid) {
+int launch_split_pass_big(gb_handle* h, const PassArgs& a, int grid, cudaStream_t stream) {
     static bool configured = false;
     if (!configured) {
         GB_CUDA(cudaFuncSetAttribute(k_fermi_split_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -921,6 +923,6 @@ int launch_split_pass_big(gb_handle* h, const PassArgs& a, int grid) {
         configured = true;
     }
     if (grid <= 0) return GB_OK;
-    GB_LAUNCH(h, k_fermi_split_big, grid, BT, SMEM_BYTES, a);
+    GB_LAUNCH_ON(h, stream, k_fermi_split_big, grid, BT, SMEM_BYTES, a);
     return GB_OK;
 }

@@ -18,6 +18,8 @@ struct gb_handle {
     int device;
     int64_t launches;  // kernels launched by the current call
     cudaEvent_t ev0, ev1;  // recursion-kernel timing (created on first use)
+    cudaStream_t aux;      // second stream for a size class run beside the others
+    cudaEvent_t ev_fork, ev_join;  // (created on first use, no timing)
     int plan_valid;        // gb_plan_autotune's cache: key (n_sub, sub_nnz, m, precision)
     int64_t plan_key[4];
     gb_plan plan;
@@ -38,8 +40,10 @@ struct gb_handle {
 // Launch bookkeeping: every kernel launch goes through GB_LAUNCH so the
 // report can state how many kernels a call issued.
 #define GB_LAUNCH(h, kernel, grid, block, smem, ...)                                  \
+    GB_LAUNCH_ON(h, (h)->stream, kernel, grid, block, smem, __VA_ARGS__)
+#define GB_LAUNCH_ON(h, st, kernel, grid, block, smem, ...)                           \
     do {                                                                              \
-        kernel<<<(grid), (block), (smem), (h)->stream>>>(__VA_ARGS__);                \
+        kernel<<<(grid), (block), (smem), (st)>>>(__VA_ARGS__);                       \
         (h)->launches++;                                                              \
         cudaError_t e_ = cudaGetLastError();                                          \
         if (e_ != cudaSuccess) return GB_ERR_DEVICE;                                  \

@@ -462,6 +462,8 @@ __global__ void __launch_bounds__(FP64_THREADS) k_fermi_fp64(PassArgs a) {
                 else if (slot >= TR_D1LAM) v += -0.5 * Z1[slot - TR_D1LAM][kk];
             }
             if (slot == TR_FLOPS && threadIdx.x == 0) v = pass_gemm_flops(n, s, a.ns_iters, a.m);
+            if (slot == TR_FLOPS_S && threadIdx.x == 0)
+                v = pass_flops_per_step_count(n, (int)(c1 - c0), s, a.ns_iters, a.m);
             if (slot == TR_MAXW)
                 for (int r = threadIdx.x; r < n; r += blockDim.x)
                     v = fmax(v, 0.25 * a.beta * (1.0 - Y[(int64_t)r * (n + 1)]));
@@ -745,10 +747,28 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
     GB_TRY(reduce_traces(h, n_sub, stride, L));
     double bounds[2];
     int herr = 0;
+    int32_t nclass[3] = {0, 0, 0};
     GB_CUDA(cudaMemcpyAsync(bounds, L.bounds, sizeof(bounds), cudaMemcpyDeviceToHost, st));
     GB_CUDA(cudaMemcpyAsync(&herr, L.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    GB_CUDA(cudaStreamSynchronize(st));  // one round trip for both
+    if (lists) GB_CUDA(cudaMemcpyAsync(nclass, L.work_n, sizeof(nclass), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaStreamSynchronize(st));  // one round trip for all
     if (herr) return herr;
+    // The tiled class runs beside the one-tile classes on a second stream when
+    // it holds few subgraphs (one per SM taken from the others' grid), after
+    // them when it holds many (then it fills the GPU by itself).
+    bool concurrent = false;
+    if (big) {
+        int sms = 0;
+        GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+        big_grid = nclass[2] < big_grid ? nclass[2] : big_grid;
+        concurrent = big_grid > 0 && 4 * big_grid <= sms && nclass[0] + nclass[1] > 0;
+        if (concurrent) {
+            a.grid_sms = sms - big_grid;
+            if (!h->aux) GB_CUDA(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+            if (!h->ev_fork) GB_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+            if (!h->ev_join) GB_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+        }
+    }
 
     // mu: Newton-Raphson on the core traces (Eq. NewtonRaphson), safeguarded
     // by a bisection bracket; each evaluation is one full pass.
@@ -773,6 +793,16 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
             // class takes subgraphs), the small one, the tiled one
             a.work = L.work;
             a.work_n = L.work_n;
+            PassArgs bb = a;
+            bb.work = L.work + 2 * (int64_t)n_sub;
+            bb.work_n = L.work_n + 2;
+            if (big) GB_CUDA(cudaMemsetAsync(bb.big_counter, 0, sizeof(int32_t), st));
+            if (concurrent) {
+                GB_CUDA(cudaEventRecord(h->ev_fork, st));
+                GB_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+                GB_TRY(launch_split_pass_big(h, bb, big_grid, h->aux));
+                GB_CUDA(cudaEventRecord(h->ev_join, h->aux));
+            }
             if (lists) GB_TRY(launch_split_pass_listed(h, a));
             else GB_TRY(launch_split_pass(h, a));
             if (o.split_small_npad > 0) {
@@ -781,13 +811,8 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
                 b.work_n = L.work_n + 1;
                 GB_TRY(launch_split_pass_small(h, b));
             }
-            if (big) {
-                PassArgs b = a;
-                b.work = L.work + 2 * (int64_t)n_sub;
-                b.work_n = L.work_n + 2;
-                GB_CUDA(cudaMemsetAsync(b.big_counter, 0, sizeof(int32_t), st));
-                GB_TRY(launch_split_pass_big(h, b, big_grid));
-            }
+            if (concurrent) GB_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
+            else if (big && big_grid > 0) GB_TRY(launch_split_pass_big(h, bb, big_grid, st));
         } else {
             GB_LAUNCH(h, k_fermi_fp64, sub_grid, FP64_THREADS, 0, a);
         }
@@ -865,6 +890,7 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
         rep->eps_min = bounds[0];
         rep->eps_max = bounds[1];
         rep->gemm_flops = sums[TR_FLOPS];
+        rep->gemm_flops_per_step_count = sums[TR_FLOPS_S];
         rep->pass_kernel_ms = kernel_ms;
         rep->mu_d_bound = last_bound;
         rep->kernel_launches = h->launches;

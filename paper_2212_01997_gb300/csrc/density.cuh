@@ -24,8 +24,10 @@ constexpr int GB_SPLIT_MAX_CTAS = 256;
 // d1_mu over all rows, and over the core rows, of all subgraphs.  A collected
 // element (j in S_i, k in core_i) of the PSD d1_mu is bounded by
 // sqrt(d1_mu_jj d1_mu_kk) <= sqrt(MAXW MAXWC).  The other slots are summed.
-enum TraceSlot { TR_D = 0, TR_DD = 1, TR_D1MU = 2, TR_FLOPS = 3, TR_MAXW = 4, TR_MAXWC = 5, TR_D1LAM = 6 };
-constexpr int TR_FIXED = 6;  // slots before the per-RHS d1_lambda traces
+enum TraceSlot {
+    TR_D = 0, TR_DD = 1, TR_D1MU = 2, TR_FLOPS = 3, TR_MAXW = 4, TR_MAXWC = 5, TR_FLOPS_S = 6, TR_D1LAM = 7
+};
+constexpr int TR_FIXED = 7;  // slots before the per-RHS d1_lambda traces
 __host__ __device__ __forceinline__ bool trace_slot_is_max(int k) { return k == TR_MAXW || k == TR_MAXWC; }
 
 // Matrix products one pass performs on a subgraph with s steps, J Newton-
@@ -34,6 +36,15 @@ __host__ __device__ __forceinline__ bool trace_slot_is_max(int k) { return k == 
 __host__ __device__ __forceinline__ double pass_gemm_flops(int n, int s, int J, int m) {
     double g = 4.0 + 6.0 * m + (double)s * (3.0 + 2.0 * J + 4.0 * m);
     return g * 2.0 * (double)n * (double)n * (double)n;
+}
+
+// The same work counted per recursion step as a fixed budget: (2 + 2J)
+// products for d and 3 per right-hand side for the response, plus the core
+// traces 2 n^2 n_c (Taylor start, the d1_mu square and the split terms not
+// counted).
+__host__ __device__ __forceinline__ double pass_flops_per_step_count(int n, int nc, int s, int J, int m) {
+    const double n3 = 2.0 * (double)n * (double)n * (double)n;
+    return (double)s * (2.0 + 2.0 * J) * n3 + (double)m * s * 3.0 * n3 + 2.0 * (double)n * n * nc;
 }
 
 struct PassArgs {
@@ -95,6 +106,7 @@ struct PassArgs {
     int64_t big_stride;
     int32_t big_npmax;
     int32_t* big_counter;
+    int32_t grid_sms;  // SMs a persistent launch may fill (0: all of them)
     int* err;
 };
 
@@ -127,4 +139,4 @@ int launch_split_pass_small(gb_handle* h, const PassArgs& a);
 int launch_split_gather(gb_handle* h, const PassArgs& a, float* hblk, double* hdiag);
 // the tiled configuration for round16(|S_i|) > 128 over its list (a.work),
 // one subgraph per CTA at a time, dynamically scheduled; grid CTAs
-int launch_split_pass_big(gb_handle* h, const PassArgs& a, int grid);
+int launch_split_pass_big(gb_handle* h, const PassArgs& a, int grid, cudaStream_t stream);

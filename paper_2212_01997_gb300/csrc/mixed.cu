@@ -991,6 +991,8 @@ __global__ void __launch_bounds__(THREADS, GB_SPLIT_MINB) GB_SPLIT_KERNEL(PassAr
                 if (sl == TR_D1MU) v *= a.beta;
             } else if (sl == TR_FLOPS) {
                 v = pass_gemm_flops(n, s, a.ns_iters, a.m);
+            } else if (sl == TR_FLOPS_S) {
+                v = pass_flops_per_step_count(n, ncore, s, a.ns_iters, a.m);
             } else if (sl == TR_MAXWC) {
                 float g = 0.f;
                 for (int e = 0; e < ncore; ++e) g = fmaxf(g, c.tv[T_DD][e]);
@@ -1149,6 +1151,7 @@ int GB_SPLIT_LAUNCH(gb_handle* h, const PassArgs& a) {
     }
     int sms = 0;
     GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    if (a.grid_sms > 0 && a.grid_sms < sms) sms = a.grid_sms;
     // persistent: GB_SPLIT_MINB CTAs per SM, within the response scratch
     // (min(n_sub, GB_SPLIT_MAX_CTAS) x 64 KB per RHS; a CTA takes STAGE_BYTES)
     const int64_t cap = (int64_t)(a.n_sub < GB_SPLIT_MAX_CTAS ? a.n_sub : GB_SPLIT_MAX_CTAS) * 65536 / STAGE_BYTES;

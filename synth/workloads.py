@@ -43,6 +43,8 @@ WORKLOADS = {
     # 10,000 waters, 60,000 orbitals, mixed vs FP64, kT 0.05 / 0.2, tau 1e-4 / 1e-6
     "water10k": Workload("water10k", 2, 10000, 0.2, 1e-4, precision="mixed"),
     "water10k_kT0.05": Workload("water10k_kT0.05", 2, 10000, 0.05, 1e-6, precision="mixed"),
+    "water10k_kT0.05_tau1e-4": Workload("water10k_kT0.05_tau1e-4", 2, 10000, 0.05, 1e-4, precision="mixed"),
+    "water10k_tau1e-6": Workload("water10k_tau1e-6", 2, 10000, 0.2, 1e-6, precision="mixed"),
     # 20,000 waters, 120,000 orbitals, m = 6 right-hand sides
     "water20k_m6": Workload("water20k_m6", 4, 20000, 0.1, 1e-5, m=6, precision="mixed"),
     # 30,000 atoms: 8 chains of 500 C/N/O heavy atoms with H caps, solvated

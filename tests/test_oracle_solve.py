@@ -143,3 +143,39 @@ def test_graph_invariants_and_canonical_finite_difference(water64):
     # neutral system: Mulliken charges sum to zero
     q = mulliken_charges(np.diag(D), system.orb_atom, system.z_valence)
     assert abs(q.sum()) < 1e-8
+
+
+def test_mulliken_two_atom_closed_form():
+    # two atoms with one orbital each and two electrons (one occupied
+    # orbital): at low temperature the bonding orbital (cos t, sin t) is
+    # filled, D_11 = cos^2 t, and q_1 = 1 - 2 D_11 = -(e2 - e1) / sqrt((e2 -
+    # e1)^2 + 4 h^2): the atom with the lower on-site energy is negative.  A
+    # sign error (population minus Z) or a dropped spin factor of 2 fails.
+    from oracle.solve import mulliken_charges
+    e1, e2, h = -2.0, 1.0, -0.8
+    H = np.array([[e1, h], [h, e2]])
+    full = oracle_full(H, [], 0.001, 1.0)
+    q = mulliken_charges(np.diag(full.D), np.array([0, 1]), np.array([1.0, 1.0]))
+    expect = -(e2 - e1) / np.sqrt((e2 - e1) ** 2 + 4 * h * h)
+    assert abs(q[0] - expect) < 1e-12 and abs(q[1] + expect) < 1e-12
+    assert q[0] < 0
+
+
+def test_mulliken_response_is_the_charge_derivative():
+    # q1 = -2 sum_o D1_oo is dq/dlambda of H + lambda H1 at fixed electron
+    # count: central difference of the charges themselves
+    from oracle.solve import mulliken_charges
+    rng = np.random.default_rng(5)
+    n = 12
+    A = rng.normal(size=(n, n))
+    H = 0.5 * (A + A.T) + np.diag(rng.normal(0, 2, n))
+    H1 = np.diag(rng.normal(0, 0.3, n))
+    atom = np.repeat(np.arange(4), 3)
+    z = np.array([2.0, 1.0, 2.0, 1.0])
+    kT, nocc = 0.3, 3.0
+    full = oracle_full(H, [H1], kT, nocc)
+    q1 = mulliken_charges(np.diag(full.D1[0]), atom, np.zeros(4))
+    eps = 1e-4
+    qp = mulliken_charges(np.diag(oracle_full(H + eps * H1, [], kT, nocc).D), atom, z)
+    qm = mulliken_charges(np.diag(oracle_full(H - eps * H1, [], kT, nocc).D), atom, z)
+    assert np.abs((qp - qm) / (2 * eps) - q1).max() < 1e-7
