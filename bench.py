@@ -421,6 +421,8 @@ def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world,
                                    "K, dt 0.25 fs; the headline geometry is step 0), one per step; graph from |H| "
                                    "and the previous step's D"}
 
+    if fp64_steps <= 0:
+        return out
     # the plain FP64 GPU path on the same graph and partition (same D_1), its
     # own mu; then the split path at the FP64 mu
     dp = d_1
@@ -644,9 +646,9 @@ def main():
                                 "density_and_response (warm-started mu); D_1 = first-pass density on the H "
                                 "graph")},
             "e2e": head.get("e2e"), "gpu_launches": head["launches"], "roofline": roof, "cpu_baseline": cpu,
-            "clocks": head["clocks"], "fp64_path": head["fp64"],
-            "mixed_over_fp64": head["value"] / world / head["fp64"]["value"],
-            "accuracy_vs_fp64_gpu": head["accuracy_vs_fp64_gpu"],
+            "clocks": head["clocks"], "fp64_path": head.get("fp64"),
+            "mixed_over_fp64": head["value"] / world / head["fp64"]["value"] if "fp64" in head else None,
+            "accuracy_vs_fp64_gpu": head.get("accuracy_vs_fp64_gpu"),
             "mu": head["mu"], "mu1": head["mu1"], "passes": head["passes"], "max_steps": head["max_steps"],
             "max_abs_D_minus_DT": head.get("max_abs_D_minus_DT"), "moving": head.get("moving"),
         }

@@ -255,8 +255,9 @@ int gb_partition_capped(gb_handle* h, const gb_graph* G, const int32_t* group, i
  * GB_ERR_WORKSPACE before any work.  The entry point calls no cudaMalloc,
  * cudaFree or other allocating routine.
  * The first call on a device looks up the array's device address on the
- * current device (cudaGetSymbolAddress), so make that first call before any
- * stream capture.  All calls share the one array and it keeps the last call's
+ * current device (cudaGetSymbolAddress), and so does the first call after the
+ * device's context was created again (cudaDeviceReset); make such a call
+ * before any stream capture.  All calls share the one array and it keeps the last call's
  * contents (the call clears what it needs): calls that overlap on the GPU --
  * on different streams, or from different host threads -- race and must be
  * serialised by the caller.  Synchronises the stream. */

@@ -724,6 +724,7 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
     a.big_stride = L.big_stride;
     a.big_npmax = L.big_npmax;
     a.big_counter = split ? L.work_n + 3 : nullptr;
+    a.counter = split ? L.work_n + 4 : nullptr;
     a.err = L.err;
     // spectral bounds.  Split path: the gather of the dense principal
     // submatrices of H and H1 (once per call: they do not depend on mu) also
@@ -796,19 +797,23 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
             PassArgs bb = a;
             bb.work = L.work + 2 * (int64_t)n_sub;
             bb.work_n = L.work_n + 2;
-            if (big) GB_CUDA(cudaMemsetAsync(bb.big_counter, 0, sizeof(int32_t), st));
+            // the three launches' work counters (tiled, 128-column, small)
+            GB_CUDA(cudaMemsetAsync(L.work_n + 3, 0, 3 * sizeof(int32_t), st));
             if (concurrent) {
                 GB_CUDA(cudaEventRecord(h->ev_fork, st));
                 GB_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
                 GB_TRY(launch_split_pass_big(h, bb, big_grid, h->aux));
                 GB_CUDA(cudaEventRecord(h->ev_join, h->aux));
             }
-            if (lists) GB_TRY(launch_split_pass_listed(h, a));
+            // the 128-column class: its list when the small class is in use,
+            // else every subgraph up to 128 orbitals (the kernel skips the rest)
+            if (o.split_small_npad > 0) GB_TRY(launch_split_pass_listed(h, a));
             else GB_TRY(launch_split_pass(h, a));
             if (o.split_small_npad > 0) {
                 PassArgs b = a;
                 b.work = L.work + n_sub;
                 b.work_n = L.work_n + 1;
+                b.counter = L.work_n + 5;
                 GB_TRY(launch_split_pass_small(h, b));
             }
             if (concurrent) GB_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));

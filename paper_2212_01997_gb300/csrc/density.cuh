@@ -107,6 +107,7 @@ struct PassArgs {
     int32_t big_npmax;
     int32_t* big_counter;
     int32_t grid_sms;  // SMs a persistent launch may fill (0: all of them)
+    int32_t* counter;  // the launch's dynamic work counter (zeroed before it)
     int* err;
 };
 

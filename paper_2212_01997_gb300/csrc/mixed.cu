@@ -108,6 +108,7 @@ struct __align__(16) Ctl {
     int abort;
     int s;                      // the current subgraph's step count
     int kfew;                   // steps dropped by the bound on Q
+    int32_t cur, nxt;           // claimed work items: in flight, next
     int32_t sigk[GB_MAX_RHS];   // perturbation normalisation sigma_r = 2^-sigk[r]
     int32_t cpos[NMAX];         // core vertices' positions in S_i
     int64_t ocol[NMAX];         // their columns' offsets in the collected CSC outputs
@@ -819,16 +820,36 @@ __global__ void __launch_bounds__(THREADS, GB_SPLIT_MINB) GB_SPLIT_KERNEL(PassAr
     fence_after();
     K.tbase = c.tmem_base;
 
-    // this launch's subgraphs: a size class's list, or all of them
+    // this launch's subgraphs: a size class's list, or all of them (those
+    // above NMAX belong to the tiled kernel and are skipped).  Dynamic
+    // scheduling: thread 0 claims work items from the launch's counter, one
+    // ahead of the item in flight so that its blocks can be prefetched.
 #if GB_SPLIT_LIST
     const int32_t nwork = *a.work_n;
-    for (int32_t j = blockIdx.x; j < nwork && c.abort == 0; j += gridDim.x) {
-        const int32_t i = a.work[j];
+#define GB_ITEM(j) a.work[j]
 #else
-    for (int32_t i = blockIdx.x; i < a.n_sub && c.abort == 0; i += gridDim.x) {
+    const int32_t nwork = a.n_sub;
+#define GB_ITEM(j) (j)
 #endif
+    if (threadIdx.x == 0) {
+        c.cur = atomicAdd(a.counter, 1);
+        c.nxt = atomicAdd(a.counter, 1);
+    }
+    for (bool first = true;; first = false) {
+        if (!first) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                c.cur = c.nxt;
+                c.nxt = atomicAdd(a.counter, 1);
+            }
+        }
+        __syncthreads();
+        const int32_t j = c.cur, jn = c.nxt;
+        if (j >= nwork || c.abort) break;
+        const int32_t i = GB_ITEM(j);
         const int64_t s0 = a.sub_ptr[i];
         const int n = (int)(a.sub_ptr[i + 1] - s0);
+        if (n > NMAX) continue;
         const int64_t c0 = a.core_ptr[i], c1 = a.core_ptr[i + 1];
         K.set_size(n);
         const int ncore = (int)(c1 - c0);
@@ -836,11 +857,7 @@ __global__ void __launch_bounds__(THREADS, GB_SPLIT_MINB) GB_SPLIT_KERNEL(PassAr
             c.cpos[e] = a.core_pos[c0 + e];
             c.ocol[e] = a.col_ptr[a.core_idx[c0 + e]];
         }
-#if GB_SPLIT_LIST
-        if (j + (int32_t)gridDim.x < nwork) K.prefetch_blocks(a.work[j + gridDim.x]);
-#else
-        K.prefetch_blocks(i + (int32_t)gridDim.x);
-#endif
+        if (jn < nwork) K.prefetch_blocks(GB_ITEM(jn));
         // the subgraph's scalars, once (FP64 is narrow on this part): step
         // count s, and sigma_r = 2^-k with (beta / 2) sigma max row sum |h1_r| <= 1
         if (threadIdx.x == 0) c.s = recursion_steps(a.beta, a.mu, a.eps_lo[i], a.eps_hi[i], a.min_steps);
@@ -1011,6 +1028,7 @@ __global__ void __launch_bounds__(THREADS, GB_SPLIT_MINB) GB_SPLIT_KERNEL(PassAr
         __syncthreads();
         fence_after();
     }
+#undef GB_ITEM
     fence_before();
     __syncthreads();
     fence_after();

@@ -413,9 +413,13 @@ extern "C" int gb_partition_capped(gb_handle* h, const gb_graph* G, const int32_
 // ---------------------------------------------------------------------------
 // gb_partition_noalloc: gb_partition for callers that cannot allocate device
 // memory (see include/gbqr.h).  Its scratch is a fixed file-scope device array
-// instead of the handle's workspace; it mirrors gb_partition step by step.
+// in place of the handle's workspace; the partition itself is partition_impl,
+// run through a handle on the stack whose workspace is that array.
 // ---------------------------------------------------------------------------
+#include <cuda.h>  // CUcontext (the driver entry point is looked up at run time)
+
 #include <atomic>
+#include <mutex>
 
 namespace {
 
@@ -432,20 +436,53 @@ constexpr size_t noalloc_scratch_bytes() {
 
 static __device__ __align__(256) unsigned char g_partition_scratch[noalloc_scratch_bytes()];
 
-std::atomic<void*> g_scratch_addr[NOALLOC_MAX_DEVICES];
+// The array's device address, per device, with the context it was looked up
+// in: a context created again (after cudaDeviceReset) gets a fresh lookup.
+struct ScratchAddr {
+    CUcontext ctx;
+    void* ptr;
+};
+ScratchAddr g_scratch_addr[NOALLOC_MAX_DEVICES];
+std::mutex g_scratch_mutex;
 
-// Device address of the scratch array on the current device; looked up once
-// per device (host code cannot use the symbol itself as a device pointer).
+typedef CUresult (*CtxGetCurrent)(CUcontext*);
+
+int current_context(CUcontext* ctx) {
+    static std::atomic<CtxGetCurrent> fn{nullptr};
+    CtxGetCurrent f = fn.load();
+    if (!f) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p)
+            return GB_ERR_DEVICE;
+        f = (CtxGetCurrent)p;
+        fn.store(f);
+    }
+    return f(ctx) == CUDA_SUCCESS ? GB_OK : GB_ERR_DEVICE;
+}
+
+// Device address of the scratch array on the current device (host code cannot
+// use the symbol itself as a device pointer), looked up once per device and
+// context.
 int noalloc_scratch(void** out) {
     int dev = 0;
     GB_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return GB_ERR_UNSUPPORTED;
-    void* p = g_scratch_addr[dev].load();
-    if (!p) {
+    CUcontext ctx = nullptr;
+    GB_TRY(current_context(&ctx));
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    ScratchAddr& e = g_scratch_addr[dev];
+    if (!ctx || !e.ptr || e.ctx != ctx) {
+        // (the lookup also brings up the device's primary context when no
+        // runtime call has yet)
+        void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_partition_scratch) != cudaSuccess || !p) return GB_ERR_DEVICE;
-        g_scratch_addr[dev].store(p);
+        if (!ctx) GB_TRY(current_context(&ctx));
+        e.ctx = ctx;
+        e.ptr = p;
     }
-    *out = p;
+    *out = e.ptr;
     return GB_OK;
 }
 
@@ -457,86 +494,23 @@ extern "C" int gb_partition_noalloc(void* stream, const gb_graph* G, const int32
                                     int32_t target_core_size, gb_part* P) {
     if (!G || !P) return GB_ERR_ARG;
     const int32_t n = G->n;
-    if (n <= 0 || !G->ptr || (G->nnz > 0 && !G->idx)) return GB_ERR_ARG;
-    if (P->n != n || !P->core_ptr || !P->core_idx || !P->core_pos || !P->sub_ptr) return GB_ERR_ARG;
-    if (P->sub_capacity < 0 || (P->sub_capacity > 0 && !P->sub_idx)) return GB_ERR_ARG;
-    int32_t block = 1;
-    if (group) {
-        if (n_groups <= 0) return GB_ERR_ARG;
-    } else {
-        if (target_core_size <= 0) return GB_ERR_ARG;
-        block = target_core_size;
-        n_groups = (n + block - 1) / block;
-    }
-    if (n > NOALLOC_MAX_N || n_groups > NOALLOC_MAX_N) return GB_ERR_WORKSPACE;
-
+    if (n <= 0) return GB_ERR_ARG;
+    const int32_t groups = group ? n_groups : (target_core_size > 0 ? (n + target_core_size - 1) / target_core_size : 0);
+    if (n > NOALLOC_MAX_N || groups > NOALLOC_MAX_N) return GB_ERR_WORKSPACE;
     void* scratch = nullptr;
     GB_TRY(noalloc_scratch(&scratch));
-    gb_handle hs;  // on the stack: stream and launch count only
+    gb_handle hs;  // on the stack: stream, scratch and launch count only
     hs.stream = (cudaStream_t)stream;
     hs.ws = scratch;
     hs.ws_bytes = sizeof(g_partition_scratch);
     hs.required_ws = 0;
     hs.launches = 0;
     hs.ev0 = hs.ev1 = nullptr;
+    hs.aux = nullptr;
+    hs.ev_fork = hs.ev_join = nullptr;
+    hs.plan_valid = 0;
     GB_CUDA(cudaGetDevice(&hs.device));
-    gb_handle* h = &hs;
-
-    Arena a(h->ws, h->ws_bytes);
-    PartLayout L = layout_part(a, n, n_groups);
-    if (!a.fits()) return GB_ERR_WORKSPACE;
-    cudaStream_t s = h->stream;
-    // the array keeps the previous call's contents: clear every counter first
-    GB_CUDA(cudaMemsetAsync(L.gcnt, 0, sizeof(int64_t) * (n_groups + 1), s));
-    GB_CUDA(cudaMemsetAsync(L.cursor, 0, sizeof(int64_t) * n, s));
-    GB_CUDA(cudaMemsetAsync(L.err, 0, sizeof(int) * 8, s));
-    GB_CUDA(cudaMemsetAsync(L.out_nnz, 0, sizeof(unsigned long long), s));
-    const int tb = 256;
-    GB_LAUNCH(h, k_group_count, (n + tb - 1) / tb, tb, 0, n, group, block, n_groups, L.gcnt, L.err);
-    // (out-of-range group ids are skipped by the count and reported with the
-    // core count below: one round trip)
-    GB_LAUNCH(h, k_nonempty, (n_groups + tb - 1) / tb, tb, 0, n_groups, (const int64_t*)L.gcnt, L.cidx);
-    GB_CUDA(cudaMemsetAsync(L.cidx + n_groups, 0, sizeof(int64_t), s));
-    GB_TRY(exclusive_scan_i64(h, L.cidx, L.cidx, n_groups + 1, L.scan_tmp));
-    int64_t n_sub = 0;
-    int herr = 0;
-    GB_CUDA(cudaMemcpyAsync(&n_sub, L.cidx + n_groups, sizeof(n_sub), cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaMemcpyAsync(&herr, L.err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaStreamSynchronize(s));
-    if (herr) return herr;
-    P->n_sub = (int32_t)n_sub;
-    GB_LAUNCH(h, k_core_sizes, (n_groups + tb - 1) / tb, tb, 0, n_groups, (const int64_t*)L.gcnt,
-              (const int64_t*)L.cidx, P->core_ptr);
-    GB_CUDA(cudaMemsetAsync(P->core_ptr + n_sub, 0, sizeof(int64_t), s));
-    GB_TRY(exclusive_scan_i64(h, P->core_ptr, P->core_ptr, n_sub + 1, L.scan_tmp));
-    GB_LAUNCH(h, k_core_fill, (n + tb - 1) / tb, tb, 0, n, group, block, (const int64_t*)L.cidx,
-              (const int64_t*)P->core_ptr, L.cursor, P->core_idx);
-    const size_t smem = sizeof(uint32_t) * ((n + 31) / 32);
-    GB_CUDA(cudaFuncSetAttribute(k_subgraphs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = (int)(n_sub < 152 * 16 ? n_sub : 152 * 16);
-    GB_LAUNCH(h, k_subgraphs, grid, SUB_THREADS, smem, n, (int32_t)n_sub, G->ptr, G->idx,
-              (const int64_t*)P->core_ptr, P->core_idx, L.sub_size, (const int64_t*)nullptr,
-              (int32_t*)nullptr, (int32_t*)nullptr, 0, L.err + 1);
-    GB_LAUNCH(h, k_out_nnz, ((int)n_sub + tb - 1) / tb, tb, 0, (int32_t)n_sub,
-              (const int64_t*)L.sub_size, (const int64_t*)P->core_ptr, L.out_nnz);
-    GB_CUDA(cudaMemsetAsync(L.sub_size + n_sub, 0, sizeof(int64_t), s));
-    GB_TRY(exclusive_scan_i64(h, L.sub_size, P->sub_ptr, n_sub + 1, L.scan_tmp));
-    int64_t sub_nnz = 0;
-    int32_t stats[3] = {0, 0, 0};
-    unsigned long long out_nnz = 0;
-    // one round trip for the three read-backs
-    GB_CUDA(cudaMemcpyAsync(&sub_nnz, P->sub_ptr + n_sub, sizeof(sub_nnz), cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaMemcpyAsync(stats, L.err, sizeof(stats), cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaMemcpyAsync(&out_nnz, L.out_nnz, sizeof(out_nnz), cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaStreamSynchronize(s));
-    P->sub_nnz = sub_nnz;
-    P->max_sub = stats[1];
-    P->max_core = stats[2];
-    P->out_nnz = (int64_t)out_nnz;
-    if (sub_nnz > P->sub_capacity) return GB_ERR_CAPACITY;
-    GB_LAUNCH(h, k_subgraphs, grid, SUB_THREADS, smem, n, (int32_t)n_sub, G->ptr, G->idx,
-              (const int64_t*)P->core_ptr, P->core_idx, (int64_t*)nullptr,
-              (const int64_t*)P->sub_ptr, P->sub_idx, P->core_pos, 1, L.err + 1);
-    GB_CUDA(cudaStreamSynchronize(s));
-    return GB_OK;
+    // partition_impl clears every counter it reuses (the array keeps the
+    // previous call's contents)
+    return partition_impl(&hs, G, group, n_groups, target_core_size, P, true);
 }
