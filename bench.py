@@ -433,6 +433,15 @@ def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world,
                    "ms_per_step": t64_ms, "passes": pass64[-1], "kernel_ms": statistics.mean(k64),
                    "mu": R64.mu}
     _, Rs = step("fp16x3", R64.mu, dp, max_newton=1)
+    # the eigenbasis path (FP64, per-subgraph diagonalisation, mu from
+    # eigenvalue sums) on the same graph, from a cold mu
+    _, Re, te, ke, passe, *_ = timed("eigen", 1, 1, math.nan, dp)
+    out["fp64_eigen"] = {"value": whole_job_rate(system.n_orb, max_over_ranks(statistics.mean(te), world, dist, dev),
+                                                 world) / world,
+                         "unit": "orbitals/s", "ms_per_step": statistics.mean(te), "kernel_ms": statistics.mean(ke),
+                         "mu_iterations": passe[-1], "start": "cold (mu from the spectral bracket)",
+                         "max_abs_dD_vs_fp64_recursion": float((Re.D.val - R64.D.val).abs().max().item()),
+                         "max_abs_dD1_vs_fp64_recursion": float((Re.D1[0].val - R64.D1[0].val).abs().max().item())}
     out["accuracy_vs_fp64_gpu"] = {
         "max_abs_dD": float((Dm - R64.D.val).abs().max().item()),
         "max_abs_dD1": float((D1m - R64.D1[0].val).abs().max().item()),
@@ -646,7 +655,7 @@ def main():
                                 "density_and_response (warm-started mu); D_1 = first-pass density on the H "
                                 "graph")},
             "e2e": head.get("e2e"), "gpu_launches": head["launches"], "roofline": roof, "cpu_baseline": cpu,
-            "clocks": head["clocks"], "fp64_path": head.get("fp64"),
+            "clocks": head["clocks"], "fp64_path": head.get("fp64"), "fp64_eigen_path": head.get("fp64_eigen"),
             "mixed_over_fp64": head["value"] / world / head["fp64"]["value"] if "fp64" in head else None,
             "accuracy_vs_fp64_gpu": head.get("accuracy_vs_fp64_gpu"),
             "mu": head["mu"], "mu1": head["mu1"], "passes": head["passes"], "max_steps": head["max_steps"],

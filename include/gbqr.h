@@ -50,7 +50,10 @@ typedef enum gb_precision {
     GB_PREC_FP64 = 0,    /* every product in FP64 (the plain reference GPU path)              */
     GB_PREC_FP16X3 = 1,  /* tensor-core split products hi*hi + hi*lo + lo*hi, FP16 parts,
                             FP32 accumulation in tensor memory; traces, mu, mu1 in FP64        */
-    GB_PREC_BF16X3 = 2   /* as GB_PREC_FP16X3 with BF16 parts                                  */
+    GB_PREC_BF16X3 = 2,  /* as GB_PREC_FP16X3 with BF16 parts                                  */
+    GB_PREC_EIGEN = 3    /* FP64 in the eigenbasis: each h^(i) diagonalised (Eq. SmallKS),
+                            mu from eigenvalue sums, d, d1 from Eqs. DD and ddlambda;
+                            subgraphs up to 1,024 orbitals                                     */
 } gb_precision;
 
 /* Square sparse matrix, compressed sparse rows.  [device] arrays.

@@ -14,7 +14,7 @@ GB_OK = 0
 STATUS = {0: "GB_OK", 1: "GB_ERR_ARG", 2: "GB_ERR_CAPACITY", 3: "GB_ERR_WORKSPACE",
           4: "GB_ERR_MU_BRACKET", 5: "GB_ERR_NO_CONVERGE", 6: "GB_ERR_NAN", 7: "GB_ERR_DEVICE",
           8: "GB_ERR_UNSUPPORTED", 9: "GB_ERR_TIMEOUT"}
-PRECISION = {"fp64": 0, "fp16x3": 1, "bf16x3": 2}
+PRECISION = {"fp64": 0, "fp16x3": 1, "bf16x3": 2, "eigen": 3}
 
 
 class GbError(RuntimeError):

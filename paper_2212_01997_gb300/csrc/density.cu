@@ -519,6 +519,11 @@ struct DensityLayout {
     int64_t big_stride; // bytes per CTA
     int32_t big_ctas;   // CTAs the scratch serves
     int32_t big_npmax;  // round16(max |S_i|)
+    double* eig_scratch;  // eigen: per-CTA scratch (3 max_sub^2 doubles each)
+    int64_t eig_stride;
+    double* eig_eps;      // eigen: eigenvalues and core weights (sub_nnz each)
+    double* eig_w;
+    int32_t* eig_counter;
     int64_t pool_stride;
 };
 
@@ -539,7 +544,29 @@ DensityLayout layout_density(Arena& ar, const gb_part* P, int32_t m, int precisi
     L.d1mu_val = ar.take<double>(P->out_nnz);
     L.scan_tmp = ar.take<int64_t>(scan_temp_count(n_sub + 1) + 64);
     L.err = ar.take<int>(8);
-    if (precision == GB_PREC_FP64) {
+    L.eig_scratch = nullptr;
+    L.eig_stride = 0;
+    L.eig_eps = L.eig_w = nullptr;
+    L.eig_counter = nullptr;
+    if (precision == GB_PREC_EIGEN) {
+        // eigenvectors of every subgraph (sum_i n_i^2 <= max_sub * sum_i n_i),
+        // eigenvalues, core weights, and the per-CTA scratch of the kernels
+        L.pool_stride = ((int64_t)P->max_sub * P->sub_nnz + 32 + 63) & ~(int64_t)63;
+        L.pool = ar.take<double>(L.pool_stride);
+        L.eig_eps = ar.take<double>(P->sub_nnz);
+        L.eig_w = ar.take<double>(P->sub_nnz);
+        L.eig_stride = 3 * (int64_t)P->max_sub * P->max_sub;
+        const int64_t ctas = n_sub < GB_EIG_MAX_CTAS ? n_sub : GB_EIG_MAX_CTAS;
+        L.eig_scratch = ar.take<double>(ctas * L.eig_stride);
+        L.eig_counter = ar.take<int32_t>(8);
+        L.z1pool = nullptr;
+        L.work = nullptr;
+        L.work_n = nullptr;
+        L.hblk = nullptr;
+        L.hdiag = nullptr;
+        L.h1max = nullptr;
+        L.big = nullptr;
+    } else if (precision == GB_PREC_FP64) {
         // sum_i n_i^2 <= max_sub * sum_i n_i
         L.pool_stride = ((int64_t)P->max_sub * P->sub_nnz + 32 + 63) & ~(int64_t)63;
         L.pool = ar.take<double>((NBUF + m) * L.pool_stride);
@@ -630,9 +657,11 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
     }
     gb_opts o = {GB_PREC_FP64, 40, 0.0, 6, 0, 0.0, 0};
     if (opts) o = *opts;
-    if (o.precision < GB_PREC_FP64 || o.precision > GB_PREC_BF16X3) return GB_ERR_ARG;
+    if (o.precision < GB_PREC_FP64 || o.precision > GB_PREC_EIGEN) return GB_ERR_ARG;
     if (o.split_small_npad < 0 || o.split_small_npad > 64 || o.split_small_npad % 16 != 0) return GB_ERR_ARG;
-    const bool split = o.precision != GB_PREC_FP64;
+    const bool eigen = o.precision == GB_PREC_EIGEN;
+    const bool split = o.precision == GB_PREC_FP16X3 || o.precision == GB_PREC_BF16X3;
+    if (eigen && P->max_sub > GB_EIG_MAX_N) return GB_ERR_UNSUPPORTED;
     if (o.max_newton <= 0) o.max_newton = 40;
     if (o.min_steps <= 0) o.min_steps = 6;
     if (o.ns_iters <= 0) o.ns_iters = split ? 2 : 3;
@@ -783,13 +812,37 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
         GB_CUDA(cudaEventCreate(&h->ev1));
     }
     cudaEvent_t ev0 = h->ev0, ev1 = h->ev1;
+    EigArgs ea;
+    memset(&ea, 0, sizeof(ea));
+    if (eigen) {
+        // diagonalise every subgraph once; mu then needs only eigenvalue sums
+        ea.scratch = L.eig_scratch;
+        ea.scratch_stride = L.eig_stride;
+        ea.eps = L.eig_eps;
+        ea.w = L.eig_w;
+        ea.vt = L.pool;
+        ea.counter = L.eig_counter;
+        ea.a = a;
+        GB_CUDA(cudaEventRecord(ev0, st));
+        GB_TRY(launch_eigen(h, ea, 0));
+        GB_CUDA(cudaEventRecord(ev1, st));
+        GB_CUDA(cudaMemcpyAsync(&herr, L.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GB_CUDA(cudaStreamSynchronize(st));
+        if (herr) return herr;
+        float ms = 0.f;
+        GB_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+        kernel_ms += ms;
+    }
     int passes = 0;
     bool converged = false;
     double prev_resid = INFINITY, last_bound = INFINITY;
     for (passes = 1; passes <= o.max_newton; ++passes) {
         a.mu = mu;
         GB_CUDA(cudaEventRecord(ev0, st));
-        if (split) {
+        if (eigen) {
+            ea.a = a;
+            GB_TRY(launch_eigen(h, ea, 1));
+        } else if (split) {
             // the 128-column configuration (for its size class when another
             // class takes subgraphs), the small one, the tiled one
             a.work = L.work;
@@ -859,6 +912,23 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
         // a Newton step stays inside the bracket and within 20 kT, else bisect
         if (!(next > lo && next < hi) || fabs(next - mu) > 20.0 * kT) next = 0.5 * (lo + hi);
         mu = next;
+    }
+    if (eigen) {
+        // core columns of d, d1_mu and d1_lambda at the final mu, and the
+        // d1_lambda traces for mu_1
+        a.mu = mu;
+        ea.a = a;
+        GB_CUDA(cudaEventRecord(ev0, st));
+        GB_TRY(launch_eigen(h, ea, 2));
+        GB_CUDA(cudaEventRecord(ev1, st));
+        GB_TRY(reduce_traces(h, n_sub, stride, L));
+        GB_CUDA(cudaMemcpyAsync(sums, L.sums, sizeof(double) * stride, cudaMemcpyDeviceToHost, st));
+        GB_CUDA(cudaMemcpyAsync(&herr, L.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GB_CUDA(cudaStreamSynchronize(st));
+        float ms = 0.f;
+        GB_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+        kernel_ms += ms;
+        if (herr) return herr;
     }
     *mu_inout = mu;
     // mu_1 (Eq. dmu_1) and D1 = d1_lambda + mu_1 d1_mu

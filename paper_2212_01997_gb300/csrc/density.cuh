@@ -14,6 +14,8 @@ constexpr int GB_BIG_MAX_N = 2048;   // largest subgraph of the tiled tensor-cor
 constexpr int GB_BIG_IMAGES_FIXED = 16;  // + 2 per right-hand side
 constexpr int GB_BIG_F32 = 4;
 constexpr int GB_BIG_MAX_CTAS = 160;
+constexpr int GB_EIG_MAX_N = 1024;    // largest subgraph of the eigenbasis path
+constexpr int GB_EIG_MAX_CTAS = 608;  // its CTAs (4 per SM), each with 3 n_max^2 doubles of scratch
 // sizes the response scratch of the persistent tensor-core kernels: 64 KB per
 // RHS for each of up to this many 128-column CTAs (a small-configuration CTA
 // takes 32 KB, so twice as many of those fit)
@@ -138,6 +140,22 @@ int launch_split_pass(gb_handle* h, const PassArgs& a);
 int launch_split_pass_listed(gb_handle* h, const PassArgs& a);
 int launch_split_pass_small(gb_handle* h, const PassArgs& a);
 int launch_split_gather(gb_handle* h, const PassArgs& a, float* hblk, double* hdiag);
+// The eigenbasis path: per-CTA scratch (3 n_max^2 doubles), the eigenvalues
+// and core weights (at sub_ptr[i]) and eigenvectors (eigenvector-major, n_i^2
+// at moff[i]) of every subgraph, and a work counter.
+struct EigArgs {
+    PassArgs a;
+    double* scratch;
+    int64_t scratch_stride;
+    double* eps;
+    double* w;
+    double* vt;
+    int32_t* counter;
+};
+// which = 0: diagonalise every subgraph; 1: trace terms at a.mu from the
+// eigenvalues; 2: core columns of d, d1_mu, d1_lambda at a.mu
+int launch_eigen(gb_handle* h, const EigArgs& ea, int which);
+
 // the tiled configuration for round16(|S_i|) > 128 over its list (a.work),
 // one subgraph per CTA at a time, dynamically scheduled; grid CTAs
 int launch_split_pass_big(gb_handle* h, const PassArgs& a, int grid, cudaStream_t stream);

@@ -1,0 +1,524 @@
+// The eigenbasis (molecular-orbital) route of the graph method in FP64: every
+// subgraph's principal submatrix h^(i) is diagonalised (Eq. SmallKS), the
+// shared chemical potential follows from eigenvalue sums weighted by the
+// eigenvectors' core parts (Eq. NewtonRaphson and the terms after it), and the
+// core columns of d^(i) (Eqs. DD0, DD), of d1_mu^(i) = beta d (I - d) (Eq.
+// dddmu) and of the response d1_lambda^(i) (Eq. ddlambda) are formed in the
+// eigenbasis:
+//   d        = V diag(f) V^T,                 f_k = 1 / (exp(beta (e_k - mu)) + 1)
+//   d1_mu    = V diag(beta f (1 - f)) V^T
+//   d1_lambda= V (F o (V^T h1 V)) V^T,         F_kl = (f_k - f_l) / (e_k - e_l)
+// (F_kk = -beta f_k (1 - f_k)).  Once the subgraphs are diagonalised, every mu
+// iteration costs only the eigenvalue sums.
+//
+// Diagonalisation, one CTA per subgraph (textbook methods written out here):
+// Householder reduction of h to tridiagonal form T = Q^T h Q, the product
+// Q^T accumulated backwards, then the implicit QL iteration with Wilkinson
+// shifts on T; thread 0 runs each sweep's scalar recurrence and records its
+// plane rotations, which all threads then apply to the eigenvector rows.
+// Eigenvectors are stored eigenvector-major (Vt[k][r] = component r of
+// eigenvector k), so that the parallel updates of the rotations and of the
+// core columns read consecutive addresses across a warp.
+#include <math.h>
+
+#include "density.cuh"
+
+namespace {
+
+constexpr int EIG_THREADS = 256;
+constexpr int EIG_MAXIT = 60;   // QL iterations per eigenvalue
+constexpr int TS = 32;          // FP64 GEMM tile
+
+struct EigCtl {
+    double d[GB_EIG_MAX_N];      // diagonal / eigenvalues
+    double e[GB_EIG_MAX_N];      // sub-diagonal
+    double v[GB_EIG_MAX_N];      // a Householder vector
+    double rc[GB_EIG_MAX_N];     // one QL sweep's rotations: cos, sin, index
+    double rs[GB_EIG_MAX_N];
+    int32_t ri[GB_EIG_MAX_N];
+    double red[EIG_THREADS / 32];
+    int nrot;
+    int item;
+    int fail;
+};
+
+// sum over the block, the same value in every thread (fixed order); red is
+// free again on return
+__device__ __forceinline__ double block_sum(double x, double* red) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < EIG_THREADS / 32; ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+__device__ __forceinline__ int lower_bound_eig(const int32_t* a, int n, int32_t v) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// dense M[S, S] (row-major n x n) from a CSR matrix
+__device__ void gather_dense(int n, const int32_t* S, const int64_t* ptr, const int32_t* idx, const double* val,
+                             double* M) {
+    for (int64_t q = threadIdx.x; q < (int64_t)n * n; q += blockDim.x) M[q] = 0.0;
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        const int32_t g = S[r];
+        for (int64_t p = ptr[g]; p < ptr[g + 1]; ++p) {
+            const int c = lower_bound_eig(S, n, idx[p]);
+            if (c < n && S[c] == idx[p]) M[(int64_t)r * n + c] = val[p];
+        }
+    }
+    __syncthreads();
+}
+
+// C = A B (row-major n x n, no aliasing), 32 x 32 tiles through shared memory
+struct Tile {
+    double a[TS][TS + 1];
+    double b[TS][TS + 1];
+};
+__device__ void gemm_nn(int n, const double* A, const double* B, double* C, Tile& t) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int nt = (n + TS - 1) / TS;
+    for (int tile = 0; tile < nt * nt; ++tile) {
+        const int r0 = (tile / nt) * TS, c0 = (tile % nt) * TS;
+        double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+        for (int k0 = 0; k0 < n; k0 += TS) {
+            for (int q = threadIdx.x; q < TS * TS; q += EIG_THREADS) {
+                const int i = q / TS, j = q % TS;
+                t.a[i][j] = (r0 + i < n && k0 + j < n) ? A[(int64_t)(r0 + i) * n + k0 + j] : 0.0;
+                t.b[i][j] = (k0 + i < n && c0 + j < n) ? B[(int64_t)(k0 + i) * n + c0 + j] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int k = 0; k < TS; ++k) {
+                const double a0 = t.a[ty][k], a1 = t.a[ty + 16][k], b0 = t.b[k][tx], b1 = t.b[k][tx + 16];
+                acc[0][0] = fma(a0, b0, acc[0][0]);
+                acc[0][1] = fma(a0, b1, acc[0][1]);
+                acc[1][0] = fma(a1, b0, acc[1][0]);
+                acc[1][1] = fma(a1, b1, acc[1][1]);
+            }
+            __syncthreads();
+        }
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) {
+                const int r = r0 + ty + 16 * i, c = c0 + tx + 16 * j;
+                if (r < n && c < n) C[(int64_t)r * n + c] = acc[i][j];
+            }
+    }
+    __syncthreads();
+}
+
+// Householder reduction of the symmetric A (row-major, overwritten) to
+// tridiagonal form: d, e in c; the vector of step k in column k of A below
+// the diagonal, its factor in c.rc[k].
+__device__ void tridiagonalize(int n, double* A, EigCtl& c) {
+    for (int k = 0; k + 2 < n; ++k) {
+        // x = A[k+1.., k] (x1 read before the reduction's barriers, ahead of
+        // the writes below)
+        const double x1 = A[(int64_t)(k + 1) * n + k];
+        double ss = 0.0;
+        for (int i = k + 1 + threadIdx.x; i < n; i += EIG_THREADS) {
+            const double x = A[(int64_t)i * n + k];
+            ss = fma(x, x, ss);
+        }
+        const double sigma = block_sum(ss, c.red);
+        if (sigma == 0.0) {
+            if (threadIdx.x == 0) {
+                c.d[k] = A[(int64_t)k * n + k];
+                c.e[k] = 0.0;
+                c.rc[k] = 0.0;
+            }
+            for (int i = k + 1 + threadIdx.x; i < n; i += EIG_THREADS) c.v[i] = 0.0;
+            __syncthreads();
+            continue;
+        }
+        const double alpha = x1 >= 0.0 ? -sqrt(sigma) : sqrt(sigma);
+        const double vtv = 2.0 * (sigma - x1 * alpha);
+        const double tau = 2.0 / vtv;
+        for (int i = k + 1 + threadIdx.x; i < n; i += EIG_THREADS) {
+            const double vi = i == k + 1 ? x1 - alpha : A[(int64_t)i * n + k];
+            c.v[i] = vi;
+            A[(int64_t)i * n + k] = vi;  // kept for Q
+        }
+        if (threadIdx.x == 0) {
+            c.d[k] = A[(int64_t)k * n + k];
+            c.e[k] = alpha;
+            c.rc[k] = tau;
+        }
+        __syncthreads();
+        // p = tau A_sub v (column sums: coalesced across j), then K = tau v.p / 2
+        double vp = 0.0;
+        for (int j = k + 1 + threadIdx.x; j < n; j += EIG_THREADS) {
+            double p = 0.0;
+            for (int i = k + 1; i < n; ++i) p = fma(A[(int64_t)i * n + j], c.v[i], p);
+            p *= tau;
+            c.rs[j] = p;
+            vp = fma(c.v[j], p, vp);
+        }
+        const double K = 0.5 * tau * block_sum(vp, c.red);
+        for (int j = k + 1 + threadIdx.x; j < n; j += EIG_THREADS) c.rs[j] -= K * c.v[j];  // w
+        __syncthreads();
+        // A_sub -= v w^T + w v^T
+        const int m = n - k - 1;
+        for (int64_t q = threadIdx.x; q < (int64_t)m * m; q += EIG_THREADS) {
+            const int i = k + 1 + (int)(q / m), j = k + 1 + (int)(q % m);
+            A[(int64_t)i * n + j] -= c.v[i] * c.rs[j] + c.rs[i] * c.v[j];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (n >= 2) {
+            c.d[n - 2] = A[(int64_t)(n - 2) * n + n - 2];
+            c.e[n - 2] = A[(int64_t)(n - 1) * n + n - 2];
+        }
+        c.d[n - 1] = A[(int64_t)(n - 1) * n + n - 1];
+        c.e[n - 1] = 0.0;
+    }
+    __syncthreads();
+}
+
+// Vt = Q^T = H_{n-3} ... H_0 by backward accumulation (only the trailing
+// block changes at each step).  One warp per row of Vt.
+__device__ void accumulate_q(int n, const double* A, double* Vt, EigCtl& c) {
+    for (int64_t q = threadIdx.x; q < (int64_t)n * n; q += EIG_THREADS) Vt[q] = (q / n == q % n) ? 1.0 : 0.0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = n - 3; k >= 0; --k) {
+        const double tau = c.rc[k];
+        if (tau == 0.0) continue;  // (uniform: rc is in shared memory)
+        for (int i = k + 1 + threadIdx.x; i < n; i += EIG_THREADS) c.v[i] = A[(int64_t)i * n + k];
+        __syncthreads();
+        for (int r = k + 1 + warp; r < n; r += EIG_THREADS / 32) {
+            double u = 0.0;
+            for (int i = k + 1 + lane; i < n; i += 32) u = fma(Vt[(int64_t)r * n + i], c.v[i], u);
+            for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+            u *= tau;
+            for (int i = k + 1 + lane; i < n; i += 32) Vt[(int64_t)r * n + i] -= u * c.v[i];
+        }
+        __syncthreads();
+    }
+}
+
+// implicit QL with Wilkinson shifts on (d, e); rotations applied to the rows
+// of Vt.  Returns false when an eigenvalue needs more than EIG_MAXIT sweeps.
+__device__ bool ql_implicit(int n, double* Vt, EigCtl& c) {
+    for (int l = 0; l < n; ++l) {
+        int iter = 0;
+        for (;;) {
+            // thread 0: find the split point and run one sweep
+            if (threadIdx.x == 0) {
+                int m = l;
+                for (; m + 1 < n; ++m) {
+                    const double dd = fabs(c.d[m]) + fabs(c.d[m + 1]);
+                    if (fabs(c.e[m]) <= 0x1p-53 * dd) break;
+                }
+                c.nrot = 0;
+                if (m == l) {
+                    c.nrot = -1;  // eigenvalue l converged
+                } else if (++iter > EIG_MAXIT) {
+                    c.fail = 1;
+                    c.nrot = -1;
+                } else {
+                    double g = (c.d[l + 1] - c.d[l]) / (2.0 * c.e[l]);
+                    double r = hypot(g, 1.0);
+                    g = c.d[m] - c.d[l] + c.e[l] / (g + (g >= 0.0 ? r : -r));
+                    double s = 1.0, cc = 1.0, p = 0.0;
+                    bool early = false;
+                    int nr = 0;
+                    for (int i = m - 1; i >= l; --i) {
+                        const double f = s * c.e[i], b = cc * c.e[i];
+                        r = hypot(f, g);
+                        c.e[i + 1] = r;
+                        if (r == 0.0) {
+                            c.d[i + 1] -= p;
+                            c.e[m] = 0.0;
+                            early = true;
+                            break;
+                        }
+                        s = f / r;
+                        cc = g / r;
+                        g = c.d[i + 1] - p;
+                        r = (c.d[i] - g) * s + 2.0 * cc * b;
+                        p = s * r;
+                        c.d[i + 1] = g + p;
+                        g = cc * r - b;
+                        c.rc[nr] = cc;
+                        c.rs[nr] = s;
+                        c.ri[nr] = i;
+                        ++nr;
+                    }
+                    if (!early) {
+                        c.d[l] -= p;
+                        c.e[l] = g;
+                        c.e[m] = 0.0;
+                    }
+                    c.nrot = nr;
+                }
+            }
+            __syncthreads();
+            const int nr = c.nrot;
+            if (nr < 0) break;
+            // eigenvector rows i, i+1 of every rotation, in order; thread per component
+            for (int q = threadIdx.x; q < n; q += EIG_THREADS) {
+                for (int t = 0; t < nr; ++t) {
+                    const int i = c.ri[t];
+                    const double co = c.rc[t], si = c.rs[t];
+                    double* a = Vt + (int64_t)i * n + q;
+                    double* b = Vt + (int64_t)(i + 1) * n + q;
+                    const double vi = *a, vj = *b;
+                    *b = si * vi + co * vj;
+                    *a = co * vi - si * vj;
+                }
+            }
+            __syncthreads();
+        }
+        if (c.fail) return false;
+    }
+    return true;
+}
+
+// Fermi occupation and 1 - f without cancellation, x = beta (e - mu)
+__device__ __forceinline__ double occ(double x) {
+    return x >= 0.0 ? exp(-x) / (1.0 + exp(-x)) : 1.0 / (1.0 + exp(x));
+}
+// f (1 - f) = 1 / (4 cosh^2 (x / 2)) without overflow
+__device__ __forceinline__ double occ_weight(double x) {
+    const double t = exp(-fabs(x));
+    return t / ((1.0 + t) * (1.0 + t));
+}
+
+// Divided difference of the Fermi function, times beta: (f(x_k) - f(x_l)) /
+// (e_k - e_l).  Direct quotient when the arguments are apart; otherwise the
+// central Taylor form f'(m) + f'''(m) dx^2 / 24 with f' = -g/4, f''' =
+// -(g/8) (3 t^2 - 1), g = sech^2(m/2), t = tanh(m/2) (error O(dx^4)).
+__device__ __forceinline__ double fermi_dd(double xk, double xl, double beta) {
+    const double dx = xk - xl;
+    if (fabs(dx) > 1e-4) return beta * (occ(xk) - occ(xl)) / dx;
+    const double m = 0.5 * (xk + xl);
+    const double g = 4.0 * occ_weight(m);
+    const double t = tanh(0.5 * m);
+    return -0.25 * beta * g * (1.0 + (3.0 * t * t - 1.0) * dx * dx / 48.0);
+}
+
+}  // namespace
+
+namespace {
+
+__global__ void __launch_bounds__(EIG_THREADS) k_eigen(EigArgs ea) {
+    const PassArgs& a = ea.a;
+    __shared__ EigCtl c;
+    if (threadIdx.x == 0) c.fail = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) c.item = atomicAdd(ea.counter, 1);
+        __syncthreads();
+        const int32_t i = c.item;
+        if (i >= a.n_sub) break;
+        const int64_t s0 = a.sub_ptr[i];
+        const int n = (int)(a.sub_ptr[i + 1] - s0);
+        double* A = ea.scratch + (int64_t)blockIdx.x * ea.scratch_stride;
+        double* Vt = ea.vt + a.moff[i];
+        gather_dense(n, a.sub_idx + s0, a.Hptr, a.Hidx, a.Hval, A);
+        tridiagonalize(n, A, c);
+        accumulate_q(n, A, Vt, c);
+        if (!ql_implicit(n, Vt, c)) {
+            if (threadIdx.x == 0) set_error(a.err, GB_ERR_NO_CONVERGE);
+            c.fail = 0;
+        }
+        // eigenvalues and the core weights sum_{j in core} V_jk^2
+        const int64_t c0 = a.core_ptr[i], c1 = a.core_ptr[i + 1];
+        for (int k = threadIdx.x; k < n; k += EIG_THREADS) {
+            double wk = 0.0;
+            for (int64_t e = c0; e < c1; ++e) {
+                const double x = Vt[(int64_t)k * n + a.core_pos[e]];
+                wk = fma(x, x, wk);
+            }
+            ea.eps[s0 + k] = c.d[k];
+            ea.w[s0 + k] = wk;
+        }
+        if (threadIdx.x == 0) a.steps_out[i] = 0;
+    }
+}
+
+// Per-subgraph trace terms at a.mu from the eigenvalues alone (plus the
+// largest diagonal of d1_mu over all rows and over core rows, n^2 work):
+// TR_D = sum_k f_k w_k, TR_DD = sum_k f_k (1 - f_k) w_k, TR_D1MU = beta TR_DD.
+__global__ void __launch_bounds__(EIG_THREADS) k_eig_traces(EigArgs ea) {
+    const PassArgs& a = ea.a;
+    __shared__ double red[EIG_THREADS / 32];
+    __shared__ double gk[GB_EIG_MAX_N];
+    for (int32_t i = blockIdx.x; i < a.n_sub; i += gridDim.x) {
+        const int64_t s0 = a.sub_ptr[i];
+        const int n = (int)(a.sub_ptr[i + 1] - s0);
+        const double* Vt = ea.vt + a.moff[i];
+        double td = 0.0, tdd = 0.0;
+        for (int k = threadIdx.x; k < n; k += EIG_THREADS) {
+            const double x = a.beta * (ea.eps[s0 + k] - a.mu);
+            const double g = occ_weight(x);
+            gk[k] = g;
+            td = fma(occ(x), ea.w[s0 + k], td);
+            tdd = fma(g, ea.w[s0 + k], tdd);
+        }
+        td = block_sum(td, red);
+        tdd = block_sum(tdd, red);
+        // diag d1_mu_jj = beta sum_k g_k V_jk^2
+        double mx = 0.0;
+        for (int j = threadIdx.x; j < n; j += EIG_THREADS) {
+            double s = 0.0;
+            for (int k = 0; k < n; ++k) {
+                const double v = Vt[(int64_t)k * n + j];
+                s = fma(gk[k] * v, v, s);
+            }
+            mx = fmax(mx, s);
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+        __syncthreads();
+        double mxw = 0.0;
+        for (int w = 0; w < EIG_THREADS / 32; ++w) mxw = fmax(mxw, red[w]);
+        __syncthreads();
+        // over core rows
+        double mc = 0.0;
+        for (int64_t e = a.core_ptr[i] + threadIdx.x; e < a.core_ptr[i + 1]; e += EIG_THREADS) {
+            const int j = a.core_pos[e];
+            double s = 0.0;
+            for (int k = 0; k < n; ++k) {
+                const double v = Vt[(int64_t)k * n + j];
+                s = fma(gk[k] * v, v, s);
+            }
+            mc = fmax(mc, s);
+        }
+        for (int o = 16; o > 0; o >>= 1) mc = fmax(mc, __shfl_xor_sync(0xffffffffu, mc, o));
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double mcw = 0.0;
+            for (int w = 0; w < EIG_THREADS / 32; ++w) mcw = fmax(mcw, red[w]);
+            double* tr = a.tr + (int64_t)i * a.tr_stride;
+            tr[TR_D] = td;
+            tr[TR_DD] = tdd;
+            tr[TR_D1MU] = a.beta * tdd;
+            tr[TR_FLOPS] = 0.0;
+            tr[TR_FLOPS_S] = 0.0;
+            tr[TR_MAXW] = a.beta * mxw;
+            tr[TR_MAXWC] = a.beta * mcw;
+            for (int r = 0; r < a.m; ++r) tr[TR_D1LAM + r] = 0.0;
+        }
+        __syncthreads();
+    }
+}
+
+// Core columns of d, d1_mu and every d1_lambda_r at a.mu into the collected
+// outputs, and the d1_lambda core traces.
+__global__ void __launch_bounds__(EIG_THREADS) k_eig_response(EigArgs ea) {
+    const PassArgs& a = ea.a;
+    __shared__ Tile tile;
+    __shared__ double red[EIG_THREADS / 32];
+    __shared__ double fk[GB_EIG_MAX_N], gk[GB_EIG_MAX_N], yv[GB_EIG_MAX_N];
+    __shared__ int item;
+    if (threadIdx.x == 0) item = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item = atomicAdd(ea.counter, 1);
+        __syncthreads();
+        const int32_t i = item;
+        if (i >= a.n_sub) break;
+        const int64_t s0 = a.sub_ptr[i];
+        const int n = (int)(a.sub_ptr[i + 1] - s0);
+        const int32_t* S = a.sub_idx + s0;
+        const double* Vt = ea.vt + a.moff[i];
+        double* M = ea.scratch + (int64_t)blockIdx.x * ea.scratch_stride;  // h1, then F o h1'
+        double* T = M + (int64_t)n * n;
+        double* V = T + (int64_t)n * n;                                    // V = Vt^T
+        for (int k = threadIdx.x; k < n; k += EIG_THREADS) {
+            const double x = a.beta * (ea.eps[s0 + k] - a.mu);
+            fk[k] = occ(x);
+            gk[k] = a.beta * occ_weight(x);
+        }
+        __syncthreads();
+        const int64_t c0 = a.core_ptr[i], c1 = a.core_ptr[i + 1];
+        // d and d1_mu core columns: d[r][c] = sum_k Vt[k][r] f_k Vt[k][c]
+        for (int64_t e = c0; e < c1; ++e) {
+            const int cp = a.core_pos[e];
+            const int64_t o = a.col_ptr[a.core_idx[e]];
+            for (int r = threadIdx.x; r < n; r += EIG_THREADS) {
+                double sd = 0.0, sm = 0.0;
+                for (int k = 0; k < n; ++k) {
+                    const double p = Vt[(int64_t)k * n + r] * Vt[(int64_t)k * n + cp];
+                    sd = fma(fk[k], p, sd);
+                    sm = fma(gk[k], p, sm);
+                }
+                a.Dval[o + r] = sd;
+                a.d1mu_val[o + r] = sm;
+            }
+        }
+        if (a.m > 0) {
+            for (int64_t q = threadIdx.x; q < (int64_t)n * n; q += EIG_THREADS)
+                V[q] = Vt[(q % n) * n + q / n];
+            __syncthreads();
+        }
+        for (int rr = 0; rr < a.m; ++rr) {
+            gather_dense(n, S, a.H1ptr[rr], a.H1idx[rr], a.H1val[rr], M);
+            gemm_nn(n, Vt, M, T, tile);  // T = V^T h1
+            gemm_nn(n, T, V, M, tile);   // M = V^T h1 V
+            for (int64_t q = threadIdx.x; q < (int64_t)n * n; q += EIG_THREADS) {
+                const int k = (int)(q / n), l = (int)(q % n);
+                M[q] *= fermi_dd(a.beta * (ea.eps[s0 + k] - a.mu), a.beta * (ea.eps[s0 + l] - a.mu), a.beta);
+            }
+            __syncthreads();
+            double tl = 0.0;
+            for (int64_t e = c0; e < c1; ++e) {
+                const int cp = a.core_pos[e];
+                const int64_t o = a.col_ptr[a.core_idx[e]];
+                // y = (F o h1') u, u_l = V[cp][l] = Vt[l][cp]
+                for (int k = threadIdx.x; k < n; k += EIG_THREADS) {
+                    double s = 0.0;
+                    for (int l = 0; l < n; ++l) s = fma(M[(int64_t)k * n + l], Vt[(int64_t)l * n + cp], s);
+                    yv[k] = s;
+                }
+                __syncthreads();
+                for (int r = threadIdx.x; r < n; r += EIG_THREADS) {
+                    double s = 0.0;
+                    for (int k = 0; k < n; ++k) s = fma(Vt[(int64_t)k * n + r], yv[k], s);
+                    a.D1val[rr][o + r] = s;
+                    if (r == cp) tl += s;
+                }
+                __syncthreads();
+            }
+            tl = block_sum(tl, red);
+            if (threadIdx.x == 0) a.tr[(int64_t)i * a.tr_stride + TR_D1LAM + rr] = tl;
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace
+
+int launch_eigen(gb_handle* h, const EigArgs& ea, int which) {
+    int sms = 0;
+    GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    int grid = 4 * sms;
+    if (grid > ea.a.n_sub) grid = ea.a.n_sub;
+    if (which == 0) {
+        if (grid > GB_EIG_MAX_CTAS) grid = GB_EIG_MAX_CTAS;
+        GB_CUDA(cudaMemsetAsync(ea.counter, 0, sizeof(int32_t), h->stream));
+        GB_LAUNCH(h, k_eigen, grid, EIG_THREADS, 0, ea);
+    } else if (which == 1) {
+        GB_LAUNCH(h, k_eig_traces, grid, EIG_THREADS, 0, ea);
+    } else {
+        if (grid > GB_EIG_MAX_CTAS) grid = GB_EIG_MAX_CTAS;
+        GB_CUDA(cudaMemsetAsync(ea.counter, 0, sizeof(int32_t), h->stream));
+        GB_LAUNCH(h, k_eig_response, grid, EIG_THREADS, 0, ea);
+    }
+    return GB_OK;
+}
