@@ -9,8 +9,8 @@ tests and the CPU oracle import.
 """
 
 from .system import CSR, System
-from .water import water_box, water_perturbation, thermal_trajectory
+from .water import water_box, water_perturbation, thermal_trajectory, softened_coulomb_matrix
 from .workloads import WORKLOADS, make_workload
 
 __all__ = ["CSR", "System", "water_box", "water_perturbation", "thermal_trajectory",
-           "WORKLOADS", "make_workload"]
+           "WORKLOADS", "make_workload", "softened_coulomb_matrix"]

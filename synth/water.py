@@ -196,6 +196,42 @@ def softened_coulomb_potential(pos: np.ndarray, box: float, dq: np.ndarray,
     return v
 
 
+def softened_coulomb_matrix(pos: np.ndarray, box: float, cutoff: float = H1_CUTOFF) -> CSR:
+    """C_IJ = sum over periodic images of J within the cutoff of 1 / sqrt(r_IJ^2 + 1)
+    (atoms x atoms, J = I included): the charge -> on-site potential map of the
+    perturbation model, v = C dq (softened_coulomb_potential applies the same sum)."""
+    import scipy.sparse as sp
+    n = len(pos)
+    if box >= 2.0 * cutoff:
+        tree = cKDTree(pos, boxsize=box)
+        sdm = tree.sparse_distance_matrix(tree, cutoff, output_type="coo_matrix")
+        off = sdm.row != sdm.col
+        rows = np.concatenate([sdm.row[off], np.arange(n)])
+        cols = np.concatenate([sdm.col[off], np.arange(n)])
+        vals = np.concatenate([1.0 / np.sqrt(sdm.data[off] ** 2 + 1.0), np.ones(n)])
+    else:
+        nimg = int(np.ceil(cutoff / box))
+        tree = cKDTree(pos)
+        rows, cols, vals = [], [], []
+        for a in range(-nimg, nimg + 1):
+            for b in range(-nimg, nimg + 1):
+                for c in range(-nimg, nimg + 1):
+                    img = pos + np.array([a, b, c], dtype=np.float64) * box
+                    for j, nb in enumerate(tree.query_ball_point(img, cutoff)):
+                        if not nb:
+                            continue
+                        nb = np.asarray(nb)
+                        r = np.linalg.norm(pos[nb] - img[j], axis=1)
+                        rows.append(nb)
+                        cols.append(np.full(len(nb), j))
+                        vals.append(1.0 / np.sqrt(r * r + 1.0))
+        rows, cols, vals = np.concatenate(rows), np.concatenate(cols), np.concatenate(vals)
+    m = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    m.sum_duplicates()
+    m.sort_indices()
+    return CSR(n, m.indptr.astype(np.int64), m.indices.astype(np.int32), m.data.astype(np.float64))
+
+
 def water_perturbation(system: System, seed: int) -> CSR:
     """H1 = diag(v) from seeded charge fluctuations (variance 0.01, zero sum)."""
     rng = np.random.default_rng(seed)
