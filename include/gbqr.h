@@ -10,6 +10,9 @@
  *   gb_density_and_response  D, D1, mu, mu1 on the partitioned graph (Eqs. Fermi, DD0-DD, NewtonRaphson,
  *                                                                      D1, ddlambda, dddmu, dmu_1, dCollect)
  *   gb_mulliken_charges      atomic charges q, q1 from D, D1       (Sec. "Response in observables")
+ *   gb_preconditioner        subgraph preconditioner K0            (Sec. "Preconditioner for a partitioned graph")
+ *   gb_krylov_update         low-rank Krylov kernel update         (Sec. "Preconditioned Krylov Subspace
+ *                                                                      Approximation ...", steps 1-5)
  *
  * Conventions for every entry point:
  *   - Plain C types only.  Pointers marked [device] are CUDA device pointers,
@@ -335,6 +338,91 @@ size_t gb_mulliken_workspace_size(void);
 int gb_mulliken_charges(gb_handle* h, const gb_csc* D, const gb_csc* D1, int32_t m, int32_t n_atoms,
                         const int64_t* atom_ptr, const int32_t* atom_orb, const double* z_val,
                         double* q, double* q1);
+
+/* ---- the charge model of the kernel and its preconditioner -------------- *
+ * The extended-Lagrangian electronic equations of motion act on a vector n of
+ * atomic electron populations (Sec. "Approximating the kernel"): n changes H
+ * through a charge -> potential map C (atoms x atoms),
+ *   H[n] = H0 + diag_o((C (n - Z))_atom(o)),
+ * the ground state of H[n] at fixed electron count (the graph method) gives
+ * populations rho0[n]_I = 2 sum_{o in I} D_oo, and the residual is
+ * f(n) = rho0[n] - n with Jacobian J.  Cores must hold whole atoms.
+ *
+ * gb_blocks: one dense block per subgraph over its core atoms.  [device]
+ * arrays sized by the caller: atom_ptr n_sub + 1, atoms n_atoms, val_ptr
+ * n_sub + 1, val val_capacity; block k covers atoms[atom_ptr[k] ..
+ * atom_ptr[k+1]) (ascending) and is row-major at val[val_ptr[k] ..]. */
+typedef struct gb_blocks {
+    int32_t n_blocks;       /* out: blocks (= subgraphs)                              */
+    int64_t n_atoms_total;  /* out: atoms over all blocks (= n_atoms)                 */
+    int64_t val_nnz;        /* out: sum of squared block sizes                        */
+    int64_t val_capacity;   /* in: entries val can hold                               */
+    int64_t* atom_ptr;
+    int32_t* atoms;
+    int64_t* val_ptr;
+    double* val;
+} gb_blocks;
+
+/* ---- gb_preconditioner ---------------------------------------------------- *
+ * The subgraph preconditioner K0 = {k0^(k)} (Sec. "Preconditioner for a
+ * partitioned graph", Eq. PreCond).  Every subgraph is diagonalised in FP64
+ * (as GB_PREC_EIGEN) and mu solved at fixed electron count; then, in the
+ * eigenbasis, the responses of the core atoms' populations to a unit charge
+ * on each core atom j (H1 = diag_o(C[atom(o), j]) restricted to the
+ * subgraph, Eq. ddlambda) and to mu (Eq. dddmu) give
+ *   j_c = chi + rho_mu mu1^T - I,
+ * with mu1_j chosen per column so that every column of j_c sums to -1 (the
+ * core keeps its charge), and k0 = (j_c - alpha I)^-1.
+ *   H        [host] struct of [device] CSR, the Hamiltonian the kernel is for.
+ *   P, kT, n_electrons  as gb_density_and_response.
+ *   C        [host] struct of [device] CSR, atoms x atoms, columns ascending.
+ *   orb_atom [device] atom of every orbital (n).
+ *   alpha    regularisation >= 0.
+ *   mu_inout [host] initial guess (NaN: none), the solved mu on return.
+ *   K0       out (see gb_blocks); GB_ERR_CAPACITY with val_nnz set when
+ *            val_capacity is too small.
+ * Errors: GB_ERR_ARG (sizes, a core not made of whole atoms),
+ * GB_ERR_UNSUPPORTED (a subgraph above 1,024 orbitals or a core above 40
+ * atoms), GB_ERR_NAN (a singular block), and those of gb_density_and_response.
+ * Workspace: gb_preconditioner_workspace_size().  Synchronises the stream. */
+size_t gb_preconditioner_workspace_size(const gb_part* P);
+int gb_preconditioner(gb_handle* h, const gb_csr* H, const gb_part* P, double kT, double n_electrons,
+                      const gb_csr* C, const int32_t* orb_atom, int32_t n_atoms, double alpha,
+                      double* mu_inout, gb_blocks* K0);
+
+/* ---- gb_krylov_update ----------------------------------------------------- *
+ * One preconditioned low-rank Krylov approximation of the kernel acting on
+ * the residual (Sec. "Preconditioned Krylov Subspace Approximation for the
+ * electronic equations of motion", steps 1-5; Eqs. LowRankEEOM, Newton_SCF):
+ *   f = rho0[n] - n,  v_1 = K0 f / |K0 f|,
+ *   f_v_i = K0 (d rho0[n + lambda v_i] / d lambda - v_i)   (graph response to
+ *           H1 = diag(C v_i) at fixed electron count, mu_1 included),
+ *   v_{i+1} = f_v_i orthonormalised against v_1..v_i (the projection taken
+ *           twice); the expansion stops early when the remainder is below
+ *           breakdown |f_v_i| (an invariant subspace),
+ *   O_ij = f_v_i . f_v_j,  M = O^-1,
+ *   dn = -sum_ij v_i M_ij f_v_j . (K0 f)   (the Newton update n - K f).
+ *   H0, P, kT, n_electrons, C, orb_atom  as gb_preconditioner.
+ *   atom_ptr, atom_orb  [device] the orbitals of each atom (CSR), for rho0.
+ *   z, n     [device] reference populations Z and the current n (n_atoms).
+ *   K0       [host] struct of [device] blocks from gb_preconditioner, or NULL
+ *            for K0 = k0_scalar I.
+ *   m        Krylov vectors at most (1..8); breakdown > 0 (e.g. 1e-6).
+ *   opts     [host] precision etc. of the density solves (NULL: FP64).
+ *   mu_inout [host] initial guess, the ground-state mu of H[n] on return.
+ *   f, dn    out, [device] n_atoms each; v, fv out, [device] m x n_atoms
+ *            (row i = vector i; rows beyond *rank untouched).
+ *   M        out, [host] m x m (the rank x rank inverse, row-major, stride m).
+ *   rank     out, [host] vectors used.
+ * Errors: those of gb_density_and_response; GB_ERR_ARG (sizes, H0 without a
+ * diagonal entry in some row).  Workspace: gb_krylov_workspace_size().
+ * Synchronises the stream. */
+size_t gb_krylov_workspace_size(const gb_csr* H0, const gb_part* P, int32_t n_atoms, const gb_opts* opts);
+int gb_krylov_update(gb_handle* h, const gb_csr* H0, const gb_part* P, double kT, double n_electrons,
+                     const gb_csr* C, const int32_t* orb_atom, const int64_t* atom_ptr, const int32_t* atom_orb,
+                     int32_t n_atoms, const double* z, const double* n, const gb_blocks* K0, double k0_scalar,
+                     int32_t m, double breakdown, const gb_opts* opts, double* mu_inout, double* f, double* v,
+                     double* fv, double* dn, double* M, int32_t* rank);
 
 /* ---- gb_plan_autotune ----------------------------------------------------- *
  * Size bins -> kernel configuration for the split-precision recursion.  The

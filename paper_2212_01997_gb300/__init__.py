@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import ctypes as C
 import math
+from ctypes import byref as C_byref, c_double as C_double, c_int32 as C_int32
 from dataclasses import dataclass, field
 
 import torch
@@ -23,12 +24,18 @@ from . import _lib as L
 from ._lib import GbError, PRECISION
 
 __all__ = ["DeviceCSR", "Graph", "Partition", "CSC", "Result", "Handle", "graph_build", "partition",
-           "density_and_response", "mulliken_charges", "plan_autotune", "GbError", "PRECISION", "library"]
+           "density_and_response", "mulliken_charges", "preconditioner", "krylov_update", "plan_autotune",
+           "GbError", "PRECISION", "library"]
 
 
 def library():
     """The loaded libgbqr.so (raises if it has not been built)."""
     return L.load()
+
+
+def Cn(coupling: "DeviceCSR") -> int:
+    """Rows of a coupling matrix (atoms)."""
+    return int(coupling.n)
 
 
 def _ptr(t: torch.Tensor | None) -> int | None:
@@ -299,6 +306,89 @@ def mulliken_charges(D: CSC, D1: list, atom_ptr: torch.Tensor, atom_orb: torch.T
                                                              atom_orb.data_ptr(), z_val.data_ptr(), q.data_ptr(),
                                                              q1.data_ptr() if m else None))
     return q, [q1[r] for r in range(m)]
+
+
+@dataclass
+class Blocks:
+    """Block-diagonal preconditioner K0: block k over atoms[atom_ptr[k]:atom_ptr[k+1]], row-major at
+    val[val_ptr[k]:]."""
+
+    atom_ptr: torch.Tensor
+    atoms: torch.Tensor
+    val_ptr: torch.Tensor
+    val: torch.Tensor
+    mu: float
+
+    def struct(self) -> L.gb_blocks:
+        return L.gb_blocks(self.atom_ptr.numel() - 1, self.atoms.numel(), self.val.numel(), self.val.numel(),
+                           self.atom_ptr.data_ptr(), self.atoms.data_ptr(), self.val_ptr.data_ptr(),
+                           self.val.data_ptr())
+
+
+def preconditioner(H: DeviceCSR, part: Partition, kT: float, n_electrons: float, C: DeviceCSR,
+                   orb_atom: torch.Tensor, alpha: float, *, mu0: float = math.nan,
+                   handle: Handle | None = None) -> Blocks:
+    """gb_preconditioner: the subgraph preconditioner k0 = (j_c - alpha I)^-1 per core."""
+    hd = handle or _default_handle(H.ptr.device)
+    lib = hd.lib
+    dev = hd.device
+    ps = part.struct()
+    hd.workspace(lib.gb_preconditioner_workspace_size(C_byref(ps)))
+    orb_atom = orb_atom.to(device=dev, dtype=torch.int32).contiguous()
+    atom_ptr = torch.empty(part.n_sub + 1, dtype=torch.int64, device=dev)
+    atoms = torch.empty(Cn(C), dtype=torch.int32, device=dev)
+    val_ptr = torch.empty(part.n_sub + 1, dtype=torch.int64, device=dev)
+    cap = 16 * Cn(C)
+    for _ in range(3):
+        val = torch.empty(max(cap, 1), dtype=torch.float64, device=dev)
+        bl = L.gb_blocks(0, 0, 0, val.numel(), atom_ptr.data_ptr(), atoms.data_ptr(), val_ptr.data_ptr(),
+                         val.data_ptr())
+        hs, cs = H.struct(), C.struct()
+        muc = C_double(mu0)
+        st = lib.gb_preconditioner(hd.h, C_byref(hs), C_byref(ps), float(kT), float(n_electrons), C_byref(cs),
+                                   orb_atom.data_ptr(), Cn(C), float(alpha), C_byref(muc), C_byref(bl))
+        if st == 2:
+            cap = int(bl.val_nnz)
+            continue
+        L.check("gb_preconditioner", st)
+        return Blocks(atom_ptr, atoms, val_ptr, val[: bl.val_nnz], muc.value)
+    raise GbError("gb_preconditioner", 2)
+
+
+def krylov_update(H0: DeviceCSR, part: Partition, kT: float, n_electrons: float, C: DeviceCSR,
+                  orb_atom: torch.Tensor, atom_ptr: torch.Tensor, atom_orb: torch.Tensor, z: torch.Tensor,
+                  n: torch.Tensor, m: int, *, K0: Blocks | None = None, k0_scalar: float = -0.5,
+                  breakdown: float = 1e-6, precision: str = "fp64", mu0: float = math.nan,
+                  handle: Handle | None = None) -> dict:
+    """gb_krylov_update: the preconditioned low-rank Krylov update of the populations n."""
+    hd = handle or _default_handle(H0.ptr.device)
+    lib = hd.lib
+    dev = hd.device
+    na = Cn(C)
+    ps, hs, cs = part.struct(), H0.struct(), C.struct()
+    opts = L.gb_opts(PRECISION[precision], 0, 0.0, 0, 0, 0.0, 0)
+    hd.workspace(lib.gb_krylov_workspace_size(C_byref(hs), C_byref(ps), na, C_byref(opts)))
+    f = torch.empty(na, dtype=torch.float64, device=dev)
+    dn = torch.empty(na, dtype=torch.float64, device=dev)
+    v = torch.zeros((m, na), dtype=torch.float64, device=dev)
+    fv = torch.zeros((m, na), dtype=torch.float64, device=dev)
+    Mh = (C_double * (m * m))()
+    rank = C_int32(0)
+    muc = C_double(mu0)
+    conv = [t.to(device=dev).contiguous() for t in (orb_atom.to(torch.int32), atom_ptr.to(torch.int64),
+                                                    atom_orb.to(torch.int32), z.to(torch.float64),
+                                                    n.to(torch.float64))]
+    ks = K0.struct() if K0 is not None else None
+    L.check("gb_krylov_update", lib.gb_krylov_update(hd.h, C_byref(hs), C_byref(ps), float(kT), float(n_electrons),
+                                                     C_byref(cs), conv[0].data_ptr(), conv[1].data_ptr(),
+                                                     conv[2].data_ptr(), na, conv[3].data_ptr(), conv[4].data_ptr(),
+                                                     C_byref(ks) if ks is not None else None, float(k0_scalar), int(m),
+                                                     float(breakdown), C_byref(opts), C_byref(muc), f.data_ptr(),
+                                                     v.data_ptr(), fv.data_ptr(), dn.data_ptr(), Mh,
+                                                     C_byref(rank)))
+    r = rank.value
+    M = [[Mh[i * m + j] for j in range(r)] for i in range(r)]
+    return {"f": f, "v": v[:r], "fv": fv[:r], "dn": dn, "M": M, "rank": r, "mu": muc.value}
 
 
 def plan_autotune(H: DeviceCSR, H1: list, kT: float, n_electrons: float, part: Partition, mu: float, *,

@@ -66,6 +66,12 @@ class gb_plan(C.Structure):
                 ("pass_ms", C.c_double * 5), ("bin_count", C.c_int64 * 8), ("cached", C.c_int32)]
 
 
+class gb_blocks(C.Structure):
+    _fields_ = [("n_blocks", C.c_int32), ("n_atoms_total", C.c_int64), ("val_nnz", C.c_int64),
+                ("val_capacity", C.c_int64), ("atom_ptr", C.c_void_p), ("atoms", C.c_void_p),
+                ("val_ptr", C.c_void_p), ("val", C.c_void_p)]
+
+
 # every entry point declared in include/gbqr.h: (name, restype, argtypes)
 SIGNATURES = [
     ("gb_create", C.c_int, [C.POINTER(C.c_void_p), C.c_void_p]),
@@ -96,6 +102,17 @@ SIGNATURES = [
     ("gb_mulliken_workspace_size", C.c_size_t, []),
     ("gb_mulliken_charges", C.c_int, [C.c_void_p, C.POINTER(gb_csc), C.POINTER(gb_csc), C.c_int32, C.c_int32,
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("gb_preconditioner_workspace_size", C.c_size_t, [C.POINTER(gb_part)]),
+    ("gb_preconditioner", C.c_int, [C.c_void_p, C.POINTER(gb_csr), C.POINTER(gb_part), C.c_double, C.c_double,
+                                    C.POINTER(gb_csr), C.c_void_p, C.c_int32, C.c_double, C.POINTER(C.c_double),
+                                    C.POINTER(gb_blocks)]),
+    ("gb_krylov_workspace_size", C.c_size_t, [C.POINTER(gb_csr), C.POINTER(gb_part), C.c_int32,
+                                              C.POINTER(gb_opts)]),
+    ("gb_krylov_update", C.c_int, [C.c_void_p, C.POINTER(gb_csr), C.POINTER(gb_part), C.c_double, C.c_double,
+                                   C.POINTER(gb_csr), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                                   C.c_void_p, C.POINTER(gb_blocks), C.c_double, C.c_int32, C.c_double,
+                                   C.POINTER(gb_opts), C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     ("gb_plan_autotune", C.c_int, [C.c_void_p, C.POINTER(gb_csr), C.POINTER(gb_csr), C.c_int32, C.c_double,
                                    C.c_double, C.POINTER(gb_part), C.POINTER(gb_opts), C.c_double,
                                    C.POINTER(gb_csc), C.POINTER(gb_csc), C.POINTER(gb_plan)]),

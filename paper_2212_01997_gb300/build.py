@@ -26,7 +26,8 @@ SOURCES = [("api.cu", "api", []), ("graph.cu", "graph", []), ("partition.cu", "p
            ("density.cu", "density", []), ("mixed.cu", "mixed", []),
            ("mixed.cu", "mixed_listed", ["-DGB_SPLIT_LIST=1"]),
            ("mixed.cu", "mixed_small", ["-DGB_SPLIT_NPMAX=64", "-DGB_SPLIT_LIST=1"]),
-           ("big.cu", "big", []), ("charges.cu", "charges", []), ("eigen.cu", "eigen", [])]
+           ("big.cu", "big", []), ("charges.cu", "charges", []), ("eigen.cu", "eigen", []),
+           ("krylov.cu", "krylov", [])]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -555,7 +555,7 @@ DensityLayout layout_density(Arena& ar, const gb_part* P, int32_t m, int precisi
         L.pool = ar.take<double>(L.pool_stride);
         L.eig_eps = ar.take<double>(P->sub_nnz);
         L.eig_w = ar.take<double>(P->sub_nnz);
-        L.eig_stride = 3 * (int64_t)P->max_sub * P->max_sub;
+        L.eig_stride = 3 * (int64_t)P->max_sub * P->max_sub + GB_PRECOND_SCRATCH;
         const int64_t ctas = n_sub < GB_EIG_MAX_CTAS ? n_sub : GB_EIG_MAX_CTAS;
         L.eig_scratch = ar.take<double>(ctas * L.eig_stride);
         L.eig_counter = ar.take<int32_t>(8);
@@ -614,6 +614,38 @@ static int reduce_traces(gb_handle* h, int32_t n_sub, int32_t stride, const Dens
     GB_LAUNCH(h, k_reduce, nb, REDUCE_THREADS, sizeof(double) * (stride + 2) * REDUCE_THREADS, n_sub, stride,
               (const double*)L.tr, (const double*)L.eps_lo, (const double*)L.eps_hi, L.partial);
     GB_LAUNCH(h, k_reduce_final, 1, 32, 0, nb, stride, (const double*)L.partial, L.sums, L.bounds);
+    return GB_OK;
+}
+
+// The eigenbasis state the last GB_PREC_EIGEN call with this partition and m
+// left in the handle's workspace (eigenvectors, eigenvalues, core weights, the
+// per-CTA scratch), as the kernels' arguments at chemical potential mu.
+int eigen_state(gb_handle* h, const gb_part* P, int32_t m, double kT, double mu, EigArgs* out,
+                size_t* density_bytes) {
+    Arena ar(h->ws, h->ws_bytes);
+    DensityLayout L = layout_density(ar, P, m, GB_PREC_EIGEN);
+    if (!ar.fits() || !h->ws) return GB_ERR_WORKSPACE;
+    *density_bytes = ar.used();
+    memset(out, 0, sizeof(*out));
+    PassArgs& a = out->a;
+    a.n_sub = P->n_sub;
+    a.m = m;
+    a.sub_ptr = P->sub_ptr;
+    a.sub_idx = P->sub_idx;
+    a.core_ptr = P->core_ptr;
+    a.core_idx = P->core_idx;
+    a.core_pos = P->core_pos;
+    a.beta = 1.0 / kT;
+    a.mu = mu;
+    a.moff = L.moff;
+    a.tr = L.tr;
+    a.err = L.err;
+    out->scratch = L.eig_scratch;
+    out->scratch_stride = L.eig_stride;
+    out->eps = L.eig_eps;
+    out->w = L.eig_w;
+    out->vt = L.pool;
+    out->counter = L.eig_counter;
     return GB_OK;
 }
 

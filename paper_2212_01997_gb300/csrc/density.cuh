@@ -156,6 +156,31 @@ struct EigArgs {
 // eigenvalues; 2: core columns of d, d1_mu, d1_lambda at a.mu
 int launch_eigen(gb_handle* h, const EigArgs& ea, int which);
 
+// The subgraph preconditioner's inputs and outputs (see gb_preconditioner):
+// the coupling C (atoms x atoms, CSR), the orbitals' atoms, the core atoms of
+// every subgraph (atoms[atom_ptr[i] ..], ascending) and the row-major blocks
+// k0 (and, when jc is set, j_c) at val_ptr[i].
+constexpr int GB_PRECOND_MAX_ATOMS = 40;
+// per-CTA scratch of the preconditioner's small blocks: chi, rho_mu, [A | I]
+constexpr int GB_PRECOND_SCRATCH = 3 * GB_PRECOND_MAX_ATOMS * GB_PRECOND_MAX_ATOMS + GB_PRECOND_MAX_ATOMS;
+struct PrecondArgs {
+    const int64_t* Cptr;
+    const int32_t* Cidx;
+    const double* Cval;
+    const int32_t* orb_atom;
+    double alpha;
+    const int64_t* atom_ptr;
+    const int32_t* atoms;
+    const int64_t* val_ptr;
+    double* val;
+    double* jc;
+};
+int launch_eig_jacobian(gb_handle* h, const EigArgs& ea, const PrecondArgs& pa);
+// the eigenbasis state of the last GB_PREC_EIGEN call (partition P, m RHS) in
+// the handle's workspace, and the bytes its layout takes
+int eigen_state(gb_handle* h, const gb_part* P, int32_t m, double kT, double mu, EigArgs* out,
+                size_t* density_bytes);
+
 // the tiled configuration for round16(|S_i|) > 128 over its list (a.work),
 // one subgraph per CTA at a time, dynamically scheduled; grid CTAs
 int launch_split_pass_big(gb_handle* h, const PassArgs& a, int grid, cudaStream_t stream);

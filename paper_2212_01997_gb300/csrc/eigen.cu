@@ -522,3 +522,161 @@ int launch_eigen(gb_handle* h, const EigArgs& ea, int which) {
     }
     return GB_OK;
 }
+
+// ---------------------------------------------------------------------------
+// The subgraph preconditioner (Sec. "Preconditioner for a partitioned graph"):
+// per subgraph, in its eigenbasis at mu, the responses of the core atoms'
+// populations p_i = 2 sum_{o in i} d_oo to a unit charge on each core atom j
+// (the diagonal perturbation u_o = C[atom(o), j], response d1_lambda of Eq.
+// ddlambda) and to mu (d1_mu, Eq. dddmu); mu1_j such that the column sums of
+// j_c = chi + rho_mu mu1^T - I are -1 (the core keeps its charge); then
+// k0 = (j_c - alpha I)^-1 by Gauss-Jordan elimination with partial pivoting.
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void __launch_bounds__(EIG_THREADS) k_eig_jacobian(EigArgs ea, PrecondArgs pa) {
+    const PassArgs& a = ea.a;
+    __shared__ Tile tile;
+    __shared__ double red[EIG_THREADS / 32];
+    __shared__ double gk[GB_EIG_MAX_N], uv[GB_EIG_MAX_N];
+    __shared__ int32_t catom[GB_PRECOND_MAX_ATOMS];
+    __shared__ int item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item = atomicAdd(ea.counter, 1);
+        __syncthreads();
+        const int32_t i = item;
+        if (i >= a.n_sub) break;
+        const int64_t s0 = a.sub_ptr[i];
+        const int n = (int)(a.sub_ptr[i + 1] - s0);
+        const int32_t* S = a.sub_idx + s0;
+        const double* Vt = ea.vt + a.moff[i];
+        double* M = ea.scratch + (int64_t)blockIdx.x * ea.scratch_stride;
+        double* T = M + (int64_t)n * n;
+        double* V = T + (int64_t)n * n;
+        // the small blocks at the end of the CTA's scratch (GB_PRECOND_SCRATCH doubles)
+        double* chi = ea.scratch + (int64_t)(blockIdx.x + 1) * ea.scratch_stride - GB_PRECOND_SCRATCH;
+        double* rmu = chi + GB_PRECOND_MAX_ATOMS * GB_PRECOND_MAX_ATOMS;
+        double* aug = rmu + GB_PRECOND_MAX_ATOMS;
+        const int64_t a0 = pa.atom_ptr[i];
+        const int na = (int)(pa.atom_ptr[i + 1] - a0);
+        const int64_t c0 = a.core_ptr[i], c1 = a.core_ptr[i + 1];
+        for (int b = threadIdx.x; b < na; b += EIG_THREADS) catom[b] = pa.atoms[a0 + b];
+        for (int k = threadIdx.x; k < n; k += EIG_THREADS)
+            gk[k] = a.beta * occ_weight(a.beta * (ea.eps[s0 + k] - a.mu));
+        for (int64_t q = threadIdx.x; q < (int64_t)n * n; q += EIG_THREADS) V[q] = Vt[(q % n) * n + q / n];
+        for (int q = threadIdx.x; q < na * na; q += EIG_THREADS) chi[q] = 0.0;
+        __syncthreads();
+        // rho_mu: one thread per core atom, its core orbitals in order
+        for (int b = threadIdx.x; b < na; b += EIG_THREADS) {
+            double s = 0.0;
+            for (int64_t e = c0; e < c1; ++e) {
+                if (pa.orb_atom[a.core_idx[e]] != catom[b]) continue;
+                const int p = a.core_pos[e];
+                for (int k = 0; k < n; ++k) {
+                    const double v = Vt[(int64_t)k * n + p];
+                    s = fma(gk[k] * v, v, s);
+                }
+            }
+            rmu[b] = 2.0 * s;
+        }
+        for (int b = 0; b < na; ++b) {
+            // u_o = C[atom(S_o), atom j]: binary search in the coupling row
+            const int32_t j = catom[b];
+            for (int o = threadIdx.x; o < n; o += EIG_THREADS) {
+                const int32_t ao = pa.orb_atom[S[o]];
+                int64_t lo = pa.Cptr[ao], hi = pa.Cptr[ao + 1];
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (pa.Cidx[mid] < j) lo = mid + 1; else hi = mid;
+                }
+                uv[o] = (lo < pa.Cptr[ao + 1] && pa.Cidx[lo] == j) ? pa.Cval[lo] : 0.0;
+            }
+            __syncthreads();
+            // T = V^T diag(u) (rows of Vt scaled by u), M = T V = V^T diag(u) V
+            for (int64_t q = threadIdx.x; q < (int64_t)n * n; q += EIG_THREADS) T[q] = Vt[q] * uv[q % n];
+            __syncthreads();
+            gemm_nn(n, T, V, M, tile);
+            for (int64_t q = threadIdx.x; q < (int64_t)n * n; q += EIG_THREADS) {
+                const int k = (int)(q / n), l = (int)(q % n);
+                M[q] *= fermi_dd(a.beta * (ea.eps[s0 + k] - a.mu), a.beta * (ea.eps[s0 + l] - a.mu), a.beta);
+            }
+            __syncthreads();
+            // d1_lambda_pp = u_p^T (F o h1') u_p for every core orbital p, u_p[k] = Vt[k][p]
+            for (int64_t e = c0; e < c1; ++e) {
+                const int p = a.core_pos[e];
+                double s = 0.0;
+                for (int k = threadIdx.x; k < n; k += EIG_THREADS) {
+                    double y = 0.0;
+                    for (int l = 0; l < n; ++l) y = fma(M[(int64_t)k * n + l], Vt[(int64_t)l * n + p], y);
+                    s = fma(Vt[(int64_t)k * n + p], y, s);
+                }
+                s = block_sum(s, red);
+                if (threadIdx.x == 0) {
+                    const int32_t ao = pa.orb_atom[a.core_idx[e]];
+                    int r = 0;
+                    while (r < na && catom[r] != ao) ++r;
+                    if (r < na) chi[r * na + b] += 2.0 * s;
+                }
+            }
+            __syncthreads();
+        }
+        // j_c, then k0 = (j_c - alpha I)^-1 (thread 0; at most GB_PRECOND_MAX_ATOMS)
+        if (threadIdx.x == 0) {
+            double rs = 0.0;
+            for (int r = 0; r < na; ++r) rs += rmu[r];
+            const int w2 = 2 * na;
+            for (int b = 0; b < na; ++b) {
+                double cs = 0.0;
+                for (int r = 0; r < na; ++r) cs += chi[r * na + b];
+                const double mu1 = rs > 0.0 ? -cs / rs : 0.0;
+                for (int r = 0; r < na; ++r) {
+                    const double jc = chi[r * na + b] + rmu[r] * mu1 - (r == b ? 1.0 : 0.0);
+                    if (pa.jc) pa.jc[pa.val_ptr[i] + (int64_t)r * na + b] = jc;
+                    aug[r * w2 + b] = jc - (r == b ? pa.alpha : 0.0);
+                    aug[r * w2 + na + b] = r == b ? 1.0 : 0.0;
+                }
+            }
+            bool singular = false;
+            for (int col = 0; col < na && !singular; ++col) {
+                int piv = col;
+                for (int r = col + 1; r < na; ++r)
+                    if (fabs(aug[r * w2 + col]) > fabs(aug[piv * w2 + col])) piv = r;
+                if (aug[piv * w2 + col] == 0.0) {
+                    singular = true;
+                    break;
+                }
+                if (piv != col)
+                    for (int q = 0; q < w2; ++q) {
+                        const double t = aug[col * w2 + q];
+                        aug[col * w2 + q] = aug[piv * w2 + q];
+                        aug[piv * w2 + q] = t;
+                    }
+                const double inv = 1.0 / aug[col * w2 + col];
+                for (int q = 0; q < w2; ++q) aug[col * w2 + q] *= inv;
+                for (int r = 0; r < na; ++r) {
+                    if (r == col) continue;
+                    const double fct = aug[r * w2 + col];
+                    if (fct != 0.0)
+                        for (int q = 0; q < w2; ++q) aug[r * w2 + q] -= fct * aug[col * w2 + q];
+                }
+            }
+            if (singular) set_error(a.err, GB_ERR_NAN);
+            for (int r = 0; r < na; ++r)
+                for (int b = 0; b < na; ++b) pa.val[pa.val_ptr[i] + (int64_t)r * na + b] = aug[r * w2 + na + b];
+        }
+    }
+}
+
+}  // namespace
+
+int launch_eig_jacobian(gb_handle* h, const EigArgs& ea, const PrecondArgs& pa) {
+    int sms = 0;
+    GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    int grid = 2 * sms;
+    if (grid > ea.a.n_sub) grid = ea.a.n_sub;
+    if (grid > GB_EIG_MAX_CTAS) grid = GB_EIG_MAX_CTAS;
+    GB_CUDA(cudaMemsetAsync(ea.counter, 0, sizeof(int32_t), h->stream));
+    GB_LAUNCH(h, k_eig_jacobian, grid, EIG_THREADS, 0, ea, pa);
+    return GB_OK;
+}
