@@ -41,6 +41,7 @@ CONFIG_TEXT = ("10,000 H2O (60,000 orbitals), periodic box 66.9 A, sp tight bind
 COMPANIONS = "water10k_kT0.05,water10k_kT0.05_tau1e-4,water10k_tau1e-6"
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_fermi_split_traffic_water10k.json")
+EIG_MAX_N = 1024  # largest subgraph of the eigenbasis path (gb_density_and_response)
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2212_01997_gb300", "csrc", f) for f in ("mixed.cu", "tc.cuh")]
 
 
@@ -119,6 +120,13 @@ def parse():
                    help="the rank-m workload instead: m=6 responses along a thermal trajectory of "
                         "20,000 waters (steps/s, p50/p99 step latency)")
     p.add_argument("--geometries", type=int, default=100, help="distinct trajectory geometries")
+    p.add_argument("--refine-d1", type=float, default=0.3,
+                   help="--trajectory: FP64 redo of subgraphs with a collected |D1| entry above this "
+                        "(gb_opts.refine_d1; <= 0: off)")
+    p.add_argument("--krylov", action="store_true",
+                   help="the kernel workload instead: subgraph preconditioner and a rank-m preconditioned Krylov "
+                        "update of the charge model on the headline box")
+    p.add_argument("--rank", type=int, default=4, help="Krylov vectors (--krylov)")
     return p.parse_args()
 
 
@@ -426,7 +434,7 @@ def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world,
     # the plain FP64 GPU path on the same graph and partition (same D_1), its
     # own mu; then the split path at the FP64 mu
     dp = d_1
-    _, R64, t64, k64, pass64, *_ = timed("fp64", fp64_steps, 1, Rm.mu, dp)
+    P64, R64, t64, k64, pass64, *_ = timed("fp64", fp64_steps, 1, Rm.mu, dp)
     t64_ms = max_over_ranks(statistics.mean(t64), world, dist, dev)
     q64, q164 = charges(R64)
     out["fp64"] = {"value": whole_job_rate(system.n_orb, t64_ms, world) / world, "unit": "orbitals/s",
@@ -435,13 +443,19 @@ def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world,
     _, Rs = step("fp16x3", R64.mu, dp, max_newton=1)
     # the eigenbasis path (FP64, per-subgraph diagonalisation, mu from
     # eigenvalue sums) on the same graph, from a cold mu
-    _, Re, te, ke, passe, *_ = timed("eigen", 1, 1, math.nan, dp)
-    out["fp64_eigen"] = {"value": whole_job_rate(system.n_orb, max_over_ranks(statistics.mean(te), world, dist, dev),
-                                                 world) / world,
-                         "unit": "orbitals/s", "ms_per_step": statistics.mean(te), "kernel_ms": statistics.mean(ke),
-                         "mu_iterations": passe[-1], "start": "cold (mu from the spectral bracket)",
-                         "max_abs_dD_vs_fp64_recursion": float((Re.D.val - R64.D.val).abs().max().item()),
-                         "max_abs_dD1_vs_fp64_recursion": float((Re.D1[0].val - R64.D1[0].val).abs().max().item())}
+    if P64.max_sub > EIG_MAX_N:
+        out["fp64_eigen"] = {"skipped": f"largest subgraph {P64.max_sub} orbitals; the eigenbasis path takes "
+                                        f"subgraphs up to {EIG_MAX_N}"}
+    else:
+        _, Rc = step("eigen", math.nan, dp)  # cold: mu from the spectral bracket
+        _, Re, te, ke, passe, *_ = timed("eigen", 1, 0, Rc.mu, dp)
+        out["fp64_eigen"] = {
+            "value": whole_job_rate(system.n_orb, max_over_ranks(statistics.mean(te), world, dist, dev), world) / world,
+            "unit": "orbitals/s", "ms_per_step": statistics.mean(te), "kernel_ms": statistics.mean(ke),
+            "mu_iterations": passe[-1], "start": "warm (the previous step's mu)",
+            "cold_mu_iterations": Rc.report["passes"], "cold_kernel_ms": Rc.report["pass_kernel_ms"],
+            "max_abs_dD_vs_fp64_recursion": float((Re.D.val - R64.D.val).abs().max().item()),
+            "max_abs_dD1_vs_fp64_recursion": float((Re.D1[0].val - R64.D1[0].val).abs().max().item())}
     out["accuracy_vs_fp64_gpu"] = {
         "max_abs_dD": float((Dm - R64.D.val).abs().max().item()),
         "max_abs_dD1": float((D1m - R64.D1[0].val).abs().max().item()),
@@ -514,7 +528,7 @@ def run_trajectory(args, rank, world):
         Hd, H1d = _geometry_on_device(gb, host[g % len(host)], system.n_orb, dev)
         P = gb.partition(gb.graph_build(Hd, wl.tau, handle=handle), groups, handle=handle)
         R = gb.density_and_response(Hd, H1d, wl.kT, system.n_electrons, P, precision=precision, mu0=mu0,
-                                    handle=handle)
+                                    refine_d1=args.refine_d1, handle=handle)
         out = ([R.D.ptr.to("cpu", non_blocking=True), R.D.idx.to("cpu", non_blocking=True),
                 R.D.val.to("cpu", non_blocking=True)] + [d.val.to("cpu", non_blocking=True) for d in R.D1])
         return P, R, out
@@ -525,7 +539,7 @@ def run_trajectory(args, rank, world):
         mu = R.mu
     clocks = ClockSampler(0)
     clocks.start()
-    ms, bo = [], 0
+    ms, bo, redo_n, redo_ms = [], 0, [], []
     for k in range(steps):
         flush.zero_()
         torch.cuda.synchronize(dev)
@@ -535,6 +549,8 @@ def run_trajectory(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms.append(e0.elapsed_time(e1))
+        redo_n.append(R.report["refined"])
+        redo_ms.append(R.report["refine_ms"])
         mu, bo = R.mu, sum(t.numel() * t.element_size() for t in out)
     clk = clocks.stop()
     # the FP64 path on the last geometry, and both at its mu
@@ -546,7 +562,7 @@ def run_trajectory(args, rank, world):
     _, Rm, _ = step(g_last, "fp16x3", mu)
     Rf = gb.density_and_response(*_geometry_on_device(gb, host[g_last % len(host)], system.n_orb, dev), wl.kT,
                                  system.n_electrons, P64, precision="fp16x3", mu0=R64.mu, max_newton=1,
-                                 handle=handle, raise_on_error=False)
+                                 refine_d1=args.refine_d1, handle=handle, raise_on_error=False)
     acc = {"max_abs_dD": float((Rm.D.val - R64.D.val).abs().max().item()),
            "max_abs_dD1": max(float((a.val - b.val).abs().max().item()) for a, b in zip(Rm.D1, R64.D1)),
            "dmu": Rm.mu - R64.mu, "max_dmu1": max(abs(a - b) for a, b in zip(Rm.mu1, R64.mu1)),
@@ -572,7 +588,88 @@ def run_trajectory(args, rank, world):
             "h2d_bytes_per_step": statistics.mean(bi), "d2h_bytes_per_step": bo,
             "fp64_path": {"seconds_per_step": s64, "steps_per_s": 1.0 / s64, "passes": R64.report["passes"]},
             "mixed_over_fp64": s64 / (statistics.mean(ms) / 1e3), "accuracy_vs_fp64_gpu": acc,
-            "clocks": clk, "passes_last": R.report["passes"]}
+            "clocks": clk, "passes_last": R.report["passes"],
+            "fp64_redo": {"threshold": args.refine_d1,
+                          "rule": "subgraphs with a collected |D1| entry above the threshold recomputed in FP64 "
+                                  "(eigenbasis) at the accepted mu, inside the timed step",
+                          "subgraphs_last": R.report["refined"], "ms_last": R.report["refine_ms"],
+                          "subgraphs_mean": statistics.mean(redo_n), "ms_mean": statistics.mean(redo_ms)}}
+    print(json.dumps(line))
+
+
+def run_krylov(args):
+    """The kernel of the electronic equations of motion on the headline box: the
+    charge model H[n] = H0 + diag(C (n - Z)) (C the softened Coulomb coupling
+    within 10 A), populations n = Z + seeded zero-sum fluctuations; the subgraph
+    preconditioner K0 (FP64 eigenbasis), then rank-m preconditioned Krylov
+    updates with split-precision and with FP64 eigenbasis density solves."""
+    import numpy as np
+    import torch
+
+    import paper_2212_01997_gb300 as gb
+    from paper_2212_01997_gb300 import build as gbuild
+    from synth import make_workload, softened_coulomb_matrix
+
+    torch.cuda.set_device(0)
+    gbuild.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    handle = gb.Handle(stream, dev)
+    wl, system, _ = make_workload(args.workload, n_rhs=0)
+    C = softened_coulomb_matrix(system.positions, system.box)
+    z = system.z_valence
+    rng = np.random.default_rng(20221204 + 2000)
+    dq = rng.normal(0.0, 0.05, size=system.n_atoms)
+    n = z + dq - dq.mean()
+    H0 = gb.DeviceCSR.from_arrays(system.H.n, system.H.indptr, system.H.indices, system.H.data, dev)
+    Cd = gb.DeviceCSR.from_arrays(C.n, C.indptr, C.indices, C.data, dev)
+    oa = torch.as_tensor(system.orb_atom, device=dev)
+    aptr, aorb = atom_map(system.orb_atom)
+    P = gb.partition(gb.graph_build(H0, wl.tau, handle=handle), torch.as_tensor(system.orb_group, device=dev),
+                     handle=handle)
+    zt, nt = torch.as_tensor(z, device=dev), torch.as_tensor(n, device=dev)
+    # H[n] for the preconditioner (its ground state)
+    import scipy.sparse as sp
+    Cs = sp.csr_matrix((C.data, C.indices, C.indptr), shape=(C.n, C.n))
+    Hs = sp.csr_matrix((system.H.data, system.H.indices, system.H.indptr), shape=(system.H.n, system.H.n))
+    Hn = (Hs + sp.diags((Cs @ (n - z))[system.orb_atom])).tocsr()
+    Hnd = gb.DeviceCSR.from_arrays(Hn.shape[0], Hn.indptr, Hn.indices, Hn.data, dev)
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return r, e0.elapsed_time(e1)
+
+    K0, ms_pc = timed(lambda: gb.preconditioner(Hnd, P, wl.kT, system.n_electrons, Cd, oa, 0.3, handle=handle))
+    K0, ms_pc = timed(lambda: gb.preconditioner(Hnd, P, wl.kT, system.n_electrons, Cd, oa, 0.3, mu0=K0.mu,
+                                                handle=handle))
+    res = {}
+    for prec in ("fp16x3", "eigen"):
+        out = None
+        for _ in range(2):  # the second call is timed (mu warm-started)
+            out, ms = timed(lambda: gb.krylov_update(H0, P, wl.kT, system.n_electrons, Cd, oa, aptr, aorb, zt, nt,
+                                                     args.rank, K0=K0, precision=prec,
+                                                     mu0=out["mu"] if out else K0.mu, handle=handle))
+        res[prec] = (out, ms)
+    o16, oe = res["fp16x3"][0], res["eigen"][0]
+    line = {"metric": "ms per preconditioned rank-m Krylov update (graph responses) on the headline box",
+            "value": res["fp16x3"][1], "unit": "ms", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "dtype": "f16x3-f32acc density solves; f64 vector algebra",
+            "config": {"workload": f"{args.workload}: {system.n_orb} orbitals, {system.n_atoms} atoms, "
+                                   f"{P.n_sub} subgraphs, kT {wl.kT} eV, graph |H| > {wl.tau:g}, coupling "
+                                   f"C_IJ = 1/sqrt(r^2 + 1 A^2) within 10 A ({C.indptr[-1]} entries)",
+                       "rank": args.rank, "alpha": 0.3},
+            "rank_used": o16["rank"], "preconditioner_ms": ms_pc,
+            "fp64_eigen_update_ms": res["eigen"][1],
+            "accuracy_vs_fp64_eigen": {
+                "max_abs_df": float((o16["f"] - oe["f"]).abs().max().item()),
+                "max_abs_ddn": float((o16["dn"] - oe["dn"]).abs().max().item()),
+                "max_abs_dn": float(oe["dn"].abs().max().item()),
+                "residual_norm": float(oe["f"].norm().item())}}
     print(json.dumps(line))
 
 
@@ -586,6 +683,10 @@ def main():
     if args.trajectory:
         if rank == 0:
             run_trajectory(args, rank, world)
+        return
+    if args.krylov:
+        if rank == 0:
+            run_krylov(args)
         return
 
     import torch
@@ -659,6 +760,7 @@ def main():
             "mixed_over_fp64": head["value"] / world / head["fp64"]["value"] if "fp64" in head else None,
             "accuracy_vs_fp64_gpu": head.get("accuracy_vs_fp64_gpu"),
             "mu": head["mu"], "mu1": head["mu1"], "passes": head["passes"], "max_steps": head["max_steps"],
+
             "max_abs_D_minus_DT": head.get("max_abs_D_minus_DT"), "moving": head.get("moving"),
         }
         line["companions"] = [{

@@ -135,6 +135,18 @@ typedef struct gb_opts {
                             the rest in the 128-column one.  0: all in the 128-column one.
                             gb_plan_autotune picks it.  Results do not depend on it beyond
                             summation order in the core-column refinement.                 */
+    double refine_d1;    /* split precision, m > 0, opt-in (<= 0: off): once mu is accepted,
+                            every subgraph of at most 1,024 orbitals whose collected D1_r
+                            (any r) holds an entry with |D1| above refine_d1 is recomputed
+                            in FP64 in its eigenbasis (Eqs. SmallKS, DD, ddlambda, dddmu) at
+                            the same mu, and mu_1 is formed from the updated traces.  The
+                            split products' D1 error grows with |D1| where states lie within
+                            a few kT of mu (measured up to ~4e-5 relative on distorted water
+                            at kT 0.1, against ~1e-6 on the equilibrium boxes); 0.3 held
+                            every other entry below 6e-6 there.  Each redone subgraph costs
+                            an FP64 diagonalisation (~20 ms alone on one SM at 130
+                            orbitals), so it suits calls where many subgraphs qualify.
+                            Ignored by the FP64 and eigenbasis precisions.                  */
 } gb_opts;
 
 typedef struct gb_report {
@@ -158,6 +170,10 @@ typedef struct gb_report {
     double mu_d_bound;       /* bound on the change of D the remaining mu step would make
                                 (first order; see gb_opts.tol_d)                          */
     int64_t kernel_launches; /* kernels launched by this call                             */
+    int32_t refined;         /* subgraphs recomputed in FP64 (gb_opts.refine_d1)          */
+    int32_t refine_skipped;  /* subgraphs above the threshold but above 1,024 orbitals,
+                                left in split precision                                    */
+    double refine_ms;        /* device time of that redo (CUDA events)                    */
 } gb_report;
 
 /* ---- handle ------------------------------------------------------------ */

@@ -241,8 +241,8 @@ def partition(G: Graph, groups: torch.Tensor | None = None, n_groups: int | None
 def density_and_response(H: DeviceCSR, H1: list, kT: float, n_electrons: float, part: Partition, *,
                          precision: str = "fp64", mu0: float = math.nan, max_newton: int = 0,
                          tol_occ: float = 0.0, min_steps: int = 0, ns_iters: int = 0, tol_d: float = 0.0,
-                         split_small_npad: int = 0, out: tuple | None = None, handle: Handle | None = None,
-                         raise_on_error: bool = True) -> Result:
+                         split_small_npad: int = 0, refine_d1: float = 0.0, out: tuple | None = None,
+                         handle: Handle | None = None, raise_on_error: bool = True) -> Result:
     """gb_density_and_response: D, D1, mu, mu1 on the partitioned graph.
 
     ``out`` may pass preallocated (D, [D1...]) CSC containers to reuse.
@@ -251,7 +251,7 @@ def density_and_response(H: DeviceCSR, H1: list, kT: float, n_electrons: float, 
     lib = hd.lib
     m = len(H1)
     opts = L.gb_opts(PRECISION[precision], int(max_newton), float(tol_occ), int(min_steps), int(ns_iters),
-                     float(tol_d), int(split_small_npad))
+                     float(tol_d), int(split_small_npad), float(refine_d1))
     ps = part.struct()
     nbytes = C.c_size_t()
     L.check("gb_density_workspace_size", lib.gb_density_workspace_size(C.byref(ps), m, C.byref(opts),

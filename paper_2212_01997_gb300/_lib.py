@@ -48,7 +48,7 @@ class gb_part(C.Structure):
 class gb_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_newton", C.c_int32), ("tol_occ", C.c_double),
                 ("min_steps", C.c_int32), ("ns_iters", C.c_int32), ("tol_d", C.c_double),
-                ("split_small_npad", C.c_int32)]
+                ("split_small_npad", C.c_int32), ("refine_d1", C.c_double)]
 
 
 class gb_report(C.Structure):
@@ -58,7 +58,8 @@ class gb_report(C.Structure):
                 ("eps_min", C.c_double), ("eps_max", C.c_double), ("gemm_flops", C.c_double),
                 ("gemm_flops_per_step_count", C.c_double),
                 ("pass_kernel_ms", C.c_double), ("mu_d_bound", C.c_double),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("refined", C.c_int32), ("refine_skipped", C.c_int32),
+                ("refine_ms", C.c_double)]
 
 
 class gb_plan(C.Structure):

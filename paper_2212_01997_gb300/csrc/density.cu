@@ -275,6 +275,29 @@ __global__ void __launch_bounds__(CLASS_THREADS) k_class_lists(int32_t n_sub, co
         for (int k = 0; k < 3; ++k) work_n[k] = tot[k];
 }
 
+// Subgraphs whose collected response holds an entry |d1_lambda_r + mu1_r
+// d1_mu| above thr (at most max_n orbitals: into list; larger: counted apart).
+struct Mu1s {
+    double v[GB_MAX_RHS];
+};
+__global__ void __launch_bounds__(256) k_flag_refine(PassArgs a, Mu1s mu1, double thr, int max_n, int32_t* list,
+                                                     int32_t* count) {
+    for (int32_t i = blockIdx.x; i < a.n_sub; i += gridDim.x) {
+        const int n = (int)(a.sub_ptr[i + 1] - a.sub_ptr[i]);
+        const int64_t c0 = a.core_ptr[i], nq = (a.core_ptr[i + 1] - c0) * n;
+        bool big = false;
+        for (int64_t q = threadIdx.x; q < nq && !big; q += blockDim.x) {
+            const int64_t o = a.col_ptr[a.core_idx[c0 + q / n]] + q % n;
+            const double w = a.d1mu_val[o];
+            for (int r = 0; r < a.m; ++r) big |= fabs(a.D1val[r][o] + mu1.v[r] * w) > thr;
+        }
+        if (__syncthreads_or(big) && threadIdx.x == 0) {
+            if (n <= max_n) list[atomicAdd(&count[0], 1)] = i;
+            else atomicAdd(&count[1], 1);
+        }
+    }
+}
+
 __global__ void k_d1_fixup(int64_t nnz, double mu1, const double* d1mu, double* d1) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
          e += (int64_t)gridDim.x * blockDim.x)
@@ -524,11 +547,22 @@ struct DensityLayout {
     double* eig_eps;      // eigen: eigenvalues and core weights (sub_nnz each)
     double* eig_w;
     int32_t* eig_counter;
+    // split, m > 0: the FP64 redo of subgraphs with a large response
+    // (gb_opts.refine_d1): their list and counts, and ref_slots eigenvector
+    // slots of ref_me^2 doubles (ref_me = min(max |S_i|, GB_EIG_MAX_N)); the
+    // eig_* fields above serve it too
+    int32_t* ref_list;
+    int32_t* ref_n;
+    double* ref_vt;
+    int32_t ref_slots;
+    int32_t ref_me;
     int64_t pool_stride;
 };
 
 // CTAs of the tiled kernel: one per SM at most, within a scratch budget
 constexpr int64_t BIG_SCRATCH_BUDGET = (int64_t)24 << 30;
+// eigenvector slots and scratch of the FP64 redo (gb_opts.refine_d1)
+constexpr int64_t REFINE_BUDGET = (int64_t)1 << 30;
 
 DensityLayout layout_density(Arena& ar, const gb_part* P, int32_t m, int precision) {
     DensityLayout L;
@@ -548,6 +582,9 @@ DensityLayout layout_density(Arena& ar, const gb_part* P, int32_t m, int precisi
     L.eig_stride = 0;
     L.eig_eps = L.eig_w = nullptr;
     L.eig_counter = nullptr;
+    L.ref_list = L.ref_n = nullptr;
+    L.ref_vt = nullptr;
+    L.ref_slots = L.ref_me = 0;
     if (precision == GB_PREC_EIGEN) {
         // eigenvectors of every subgraph (sum_i n_i^2 <= max_sub * sum_i n_i),
         // eigenvalues, core weights, and the per-CTA scratch of the kernels
@@ -601,6 +638,23 @@ DensityLayout layout_density(Arena& ar, const gb_part* P, int32_t m, int precisi
             if (ctas > fit) ctas = fit > 0 ? fit : 1;
             L.big_ctas = (int32_t)ctas;
             L.big = ar.take<uint8_t>((size_t)(ctas * L.big_stride));
+        }
+        if (m > 0) {
+            const int64_t me = P->max_sub < GB_EIG_MAX_N ? P->max_sub : GB_EIG_MAX_N;
+            int64_t slots = REFINE_BUDGET / (4 * me * me * (int64_t)sizeof(double));
+            if (slots > GB_EIG_MAX_CTAS) slots = GB_EIG_MAX_CTAS;
+            if (slots > n_sub) slots = n_sub;
+            if (slots < 1) slots = 1;
+            L.ref_me = (int32_t)me;
+            L.ref_slots = (int32_t)slots;
+            L.ref_list = ar.take<int32_t>(n_sub);
+            L.ref_n = ar.take<int32_t>(8);
+            L.eig_eps = ar.take<double>(P->sub_nnz);
+            L.eig_w = ar.take<double>(P->sub_nnz);
+            L.eig_stride = 3 * me * me;
+            L.eig_scratch = ar.take<double>(slots * L.eig_stride);
+            L.ref_vt = ar.take<double>(slots * me * me);
+            L.eig_counter = ar.take<int32_t>(8);
         }
     }
     return L;
@@ -687,7 +741,7 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
             return D1[r].val ? GB_ERR_CAPACITY : GB_ERR_ARG;
         }
     }
-    gb_opts o = {GB_PREC_FP64, 40, 0.0, 6, 0, 0.0, 0};
+    gb_opts o = {GB_PREC_FP64, 40, 0.0, 6, 0, 0.0, 0, 0.0};
     if (opts) o = *opts;
     if (o.precision < GB_PREC_FP64 || o.precision > GB_PREC_EIGEN) return GB_ERR_ARG;
     if (o.split_small_npad < 0 || o.split_small_npad > 64 || o.split_small_npad % 16 != 0) return GB_ERR_ARG;
@@ -963,6 +1017,55 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
         if (herr) return herr;
     }
     *mu_inout = mu;
+    // FP64 redo of the subgraphs whose response is large (gb_opts.refine_d1):
+    // flag them by |d1_lambda + mu_1 d1_mu| with mu_1 from the split traces,
+    // diagonalise them and overwrite their core columns of d, d1_mu, d1_lambda
+    // and their traces at the same mu, in waves of the eigenvector slots
+    int32_t refined = 0, refine_skipped = 0;
+    double refine_ms = 0.0;
+    const double refine_thr = o.refine_d1;
+    if (split && m > 0 && refine_thr > 0.0 && L.ref_list) {
+        Mu1s mv;
+        memset(&mv, 0, sizeof(mv));
+        for (int r = 0; r < m; ++r) mv.v[r] = sums[TR_D1MU] > 0.0 ? -sums[TR_D1LAM + r] / sums[TR_D1MU] : 0.0;
+        a.mu = mu;
+        GB_CUDA(cudaEventRecord(ev0, st));
+        GB_CUDA(cudaMemsetAsync(L.ref_n, 0, 8 * sizeof(int32_t), st));
+        GB_LAUNCH(h, k_flag_refine, sub_grid, tb, 0, a, mv, refine_thr, GB_EIG_MAX_N, L.ref_list, L.ref_n);
+        int32_t cnt[2] = {0, 0};
+        GB_CUDA(cudaMemcpyAsync(cnt, L.ref_n, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+        GB_CUDA(cudaStreamSynchronize(st));
+        refined = cnt[0];
+        refine_skipped = cnt[1];
+        if (refined > 0) {
+            EigArgs ra;
+            memset(&ra, 0, sizeof(ra));
+            ra.a = a;
+            ra.scratch = L.eig_scratch;
+            ra.scratch_stride = L.eig_stride;
+            ra.eps = L.eig_eps;
+            ra.w = L.eig_w;
+            ra.vt = L.ref_vt;
+            ra.vt_stride = (int64_t)L.ref_me * L.ref_me;
+            ra.counter = L.eig_counter;
+            ra.list = L.ref_list;
+            for (int32_t base = 0; base < refined; base += L.ref_slots) {
+                ra.list_base = base;
+                ra.list_n = refined - base < L.ref_slots ? refined - base : L.ref_slots;
+                GB_TRY(launch_eigen(h, ra, 0));
+                GB_TRY(launch_eigen(h, ra, 2));
+            }
+            GB_TRY(reduce_traces(h, n_sub, stride, L));
+            GB_CUDA(cudaMemcpyAsync(sums, L.sums, sizeof(double) * stride, cudaMemcpyDeviceToHost, st));
+            GB_CUDA(cudaMemcpyAsync(&herr, L.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        }
+        GB_CUDA(cudaEventRecord(ev1, st));
+        GB_CUDA(cudaStreamSynchronize(st));
+        float ms = 0.f;
+        GB_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+        refine_ms = ms;
+        if (herr) return herr;
+    }
     // mu_1 (Eq. dmu_1) and D1 = d1_lambda + mu_1 d1_mu
     for (int r = 0; r < m; ++r) {
         const double den = sums[TR_D1MU];
@@ -1001,6 +1104,9 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
         rep->pass_kernel_ms = kernel_ms;
         rep->mu_d_bound = last_bound;
         rep->kernel_launches = h->launches;
+        rep->refined = refined;
+        rep->refine_skipped = refine_skipped;
+        rep->refine_ms = refine_ms;
     }
     return converged ? GB_OK : GB_ERR_NO_CONVERGE;
 }

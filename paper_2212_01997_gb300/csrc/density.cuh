@@ -151,9 +151,17 @@ struct EigArgs {
     double* w;
     double* vt;
     int32_t* counter;
+    // list mode (list != nullptr): the subgraphs list[list_base + j],
+    // j < list_n, with the eigenvectors of item j at vt + j * vt_stride;
+    // otherwise every subgraph i with its eigenvectors at vt + a.moff[i]
+    const int32_t* list;
+    int32_t list_base;
+    int32_t list_n;
+    int64_t vt_stride;
 };
-// which = 0: diagonalise every subgraph; 1: trace terms at a.mu from the
-// eigenvalues; 2: core columns of d, d1_mu, d1_lambda at a.mu
+// which = 0: diagonalise every subgraph (of the list); 1: trace terms at a.mu
+// from the eigenvalues; 2: core columns of d, d1_mu, d1_lambda at a.mu and
+// their core traces
 int launch_eigen(gb_handle* h, const EigArgs& ea, int which);
 
 // The subgraph preconditioner's inputs and outputs (see gb_preconditioner):

@@ -12,13 +12,17 @@
 // iteration costs only the eigenvalue sums.
 //
 // Diagonalisation, one CTA per subgraph (textbook methods written out here):
-// Householder reduction of h to tridiagonal form T = Q^T h Q, the product
-// Q^T accumulated backwards, then the implicit QL iteration with Wilkinson
-// shifts on T; thread 0 runs each sweep's scalar recurrence and records its
-// plane rotations, which all threads then apply to the eigenvector rows.
+// Householder reduction of h to tridiagonal form T = Q^T h Q; every
+// eigenvalue of T by bisection on Sturm counts, one eigenvalue per thread;
+// its eigenvector z_k from a twisted factorisation T - lambda_k I = N_r
+// Delta_r N_r^T at the twist r of smallest |gamma_r| (one step of inverse
+// iteration from e_r); eigenvectors of nearly equal eigenvalues orthogonalised
+// against each other (Gram-Schmidt, twice); then V = Q Z.  All of it runs in
+// parallel over the eigenvalues: GB300's FP64 pipe makes a serial scalar
+// sweep (the implicit QL iteration) far too slow per subgraph.
 // Eigenvectors are stored eigenvector-major (Vt[k][r] = component r of
-// eigenvector k), so that the parallel updates of the rotations and of the
-// core columns read consecutive addresses across a warp.
+// eigenvector k), so that the updates of the core columns read consecutive
+// addresses across a warp.
 #include <math.h>
 
 #include "density.cuh"
@@ -26,18 +30,26 @@
 namespace {
 
 constexpr int EIG_THREADS = 256;
-constexpr int EIG_MAXIT = 60;   // QL iterations per eigenvalue
 constexpr int TS = 32;          // FP64 GEMM tile
 
+// C = A B tile buffers (the GEMM runs last, over the tridiagonal's arrays)
+struct Tile {
+    double a[TS][TS + 1];
+    double b[TS][TS + 1];
+};
+
 struct EigCtl {
-    double d[GB_EIG_MAX_N];      // diagonal / eigenvalues
-    double e[GB_EIG_MAX_N];      // sub-diagonal
-    double v[GB_EIG_MAX_N];      // a Householder vector
-    double rc[GB_EIG_MAX_N];     // one QL sweep's rotations: cos, sin, index
-    double rs[GB_EIG_MAX_N];
-    int32_t ri[GB_EIG_MAX_N];
+    union {
+        struct {
+            double d[GB_EIG_MAX_N];    // diagonal of T
+            double e[GB_EIG_MAX_N];    // its sub-diagonal (e[k] = T[k+1][k])
+            double v[GB_EIG_MAX_N];    // a Householder vector; then e^2
+            double tau[GB_EIG_MAX_N];  // the Householder factors
+            double w[GB_EIG_MAX_N];    // tridiagonalisation work vector; then the eigenvalues
+        } s;
+        Tile t;
+    };
     double red[EIG_THREADS / 32];
-    int nrot;
     int item;
     int fail;
 };
@@ -79,11 +91,28 @@ __device__ void gather_dense(int n, const int32_t* S, const int64_t* ptr, const 
     __syncthreads();
 }
 
+// W = M[S, S] V for a CSR matrix M (row-major n x n V and W): one warp per
+// row, the row's entries located in the subgraph's vertex list
+__device__ void sparse_times(int n, const int32_t* S, const int64_t* ptr, const int32_t* idx, const double* val,
+                             const double* V, double* W) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r = warp; r < n; r += EIG_THREADS / 32) {
+        const int32_t g = S[r];
+        const int64_t p0 = ptr[g], p1 = ptr[g + 1];
+        for (int l0 = 0; l0 < n; l0 += 32) {
+            const int l = l0 + lane;
+            double s = 0.0;
+            for (int64_t p = p0; p < p1; ++p) {
+                const int c = lower_bound_eig(S, n, idx[p]);
+                if (c < n && S[c] == idx[p] && l < n) s = fma(val[p], V[(int64_t)c * n + l], s);
+            }
+            if (l < n) W[(int64_t)r * n + l] = s;
+        }
+    }
+    __syncthreads();
+}
+
 // C = A B (row-major n x n, no aliasing), 32 x 32 tiles through shared memory
-struct Tile {
-    double a[TS][TS + 1];
-    double b[TS][TS + 1];
-};
 __device__ void gemm_nn(int n, const double* A, const double* B, double* C, Tile& t) {
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int nt = (n + TS - 1) / TS;
@@ -132,11 +161,11 @@ __device__ void tridiagonalize(int n, double* A, EigCtl& c) {
         const double sigma = block_sum(ss, c.red);
         if (sigma == 0.0) {
             if (threadIdx.x == 0) {
-                c.d[k] = A[(int64_t)k * n + k];
-                c.e[k] = 0.0;
-                c.rc[k] = 0.0;
+                c.s.d[k] = A[(int64_t)k * n + k];
+                c.s.e[k] = 0.0;
+                c.s.tau[k] = 0.0;
             }
-            for (int i = k + 1 + threadIdx.x; i < n; i += EIG_THREADS) c.v[i] = 0.0;
+            for (int i = k + 1 + threadIdx.x; i < n; i += EIG_THREADS) c.s.v[i] = 0.0;
             __syncthreads();
             continue;
         }
@@ -145,42 +174,42 @@ __device__ void tridiagonalize(int n, double* A, EigCtl& c) {
         const double tau = 2.0 / vtv;
         for (int i = k + 1 + threadIdx.x; i < n; i += EIG_THREADS) {
             const double vi = i == k + 1 ? x1 - alpha : A[(int64_t)i * n + k];
-            c.v[i] = vi;
+            c.s.v[i] = vi;
             A[(int64_t)i * n + k] = vi;  // kept for Q
         }
         if (threadIdx.x == 0) {
-            c.d[k] = A[(int64_t)k * n + k];
-            c.e[k] = alpha;
-            c.rc[k] = tau;
+            c.s.d[k] = A[(int64_t)k * n + k];
+            c.s.e[k] = alpha;
+            c.s.tau[k] = tau;
         }
         __syncthreads();
         // p = tau A_sub v (column sums: coalesced across j), then K = tau v.p / 2
         double vp = 0.0;
         for (int j = k + 1 + threadIdx.x; j < n; j += EIG_THREADS) {
             double p = 0.0;
-            for (int i = k + 1; i < n; ++i) p = fma(A[(int64_t)i * n + j], c.v[i], p);
+            for (int i = k + 1; i < n; ++i) p = fma(A[(int64_t)i * n + j], c.s.v[i], p);
             p *= tau;
-            c.rs[j] = p;
-            vp = fma(c.v[j], p, vp);
+            c.s.w[j] = p;
+            vp = fma(c.s.v[j], p, vp);
         }
         const double K = 0.5 * tau * block_sum(vp, c.red);
-        for (int j = k + 1 + threadIdx.x; j < n; j += EIG_THREADS) c.rs[j] -= K * c.v[j];  // w
+        for (int j = k + 1 + threadIdx.x; j < n; j += EIG_THREADS) c.s.w[j] -= K * c.s.v[j];  // w
         __syncthreads();
         // A_sub -= v w^T + w v^T
         const int m = n - k - 1;
         for (int64_t q = threadIdx.x; q < (int64_t)m * m; q += EIG_THREADS) {
             const int i = k + 1 + (int)(q / m), j = k + 1 + (int)(q % m);
-            A[(int64_t)i * n + j] -= c.v[i] * c.rs[j] + c.rs[i] * c.v[j];
+            A[(int64_t)i * n + j] -= c.s.v[i] * c.s.w[j] + c.s.w[i] * c.s.v[j];
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         if (n >= 2) {
-            c.d[n - 2] = A[(int64_t)(n - 2) * n + n - 2];
-            c.e[n - 2] = A[(int64_t)(n - 1) * n + n - 2];
+            c.s.d[n - 2] = A[(int64_t)(n - 2) * n + n - 2];
+            c.s.e[n - 2] = A[(int64_t)(n - 1) * n + n - 2];
         }
-        c.d[n - 1] = A[(int64_t)(n - 1) * n + n - 1];
-        c.e[n - 1] = 0.0;
+        c.s.d[n - 1] = A[(int64_t)(n - 1) * n + n - 1];
+        c.s.e[n - 1] = 0.0;
     }
     __syncthreads();
 }
@@ -192,97 +221,238 @@ __device__ void accumulate_q(int n, const double* A, double* Vt, EigCtl& c) {
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int k = n - 3; k >= 0; --k) {
-        const double tau = c.rc[k];
+        const double tau = c.s.tau[k];
         if (tau == 0.0) continue;  // (uniform: rc is in shared memory)
-        for (int i = k + 1 + threadIdx.x; i < n; i += EIG_THREADS) c.v[i] = A[(int64_t)i * n + k];
+        for (int i = k + 1 + threadIdx.x; i < n; i += EIG_THREADS) c.s.v[i] = A[(int64_t)i * n + k];
         __syncthreads();
         for (int r = k + 1 + warp; r < n; r += EIG_THREADS / 32) {
             double u = 0.0;
-            for (int i = k + 1 + lane; i < n; i += 32) u = fma(Vt[(int64_t)r * n + i], c.v[i], u);
+            for (int i = k + 1 + lane; i < n; i += 32) u = fma(Vt[(int64_t)r * n + i], c.s.v[i], u);
             for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
             u *= tau;
-            for (int i = k + 1 + lane; i < n; i += 32) Vt[(int64_t)r * n + i] -= u * c.v[i];
+            for (int i = k + 1 + lane; i < n; i += 32) Vt[(int64_t)r * n + i] -= u * c.s.v[i];
         }
         __syncthreads();
     }
 }
 
-// implicit QL with Wilkinson shifts on (d, e); rotations applied to the rows
-// of Vt.  Returns false when an eigenvalue needs more than EIG_MAXIT sweeps.
-__device__ bool ql_implicit(int n, double* Vt, EigCtl& c) {
-    for (int l = 0; l < n; ++l) {
-        int iter = 0;
-        for (;;) {
-            // thread 0: find the split point and run one sweep
-            if (threadIdx.x == 0) {
-                int m = l;
-                for (; m + 1 < n; ++m) {
-                    const double dd = fabs(c.d[m]) + fabs(c.d[m + 1]);
-                    if (fabs(c.e[m]) <= 0x1p-53 * dd) break;
-                }
-                c.nrot = 0;
-                if (m == l) {
-                    c.nrot = -1;  // eigenvalue l converged
-                } else if (++iter > EIG_MAXIT) {
-                    c.fail = 1;
-                    c.nrot = -1;
-                } else {
-                    double g = (c.d[l + 1] - c.d[l]) / (2.0 * c.e[l]);
-                    double r = hypot(g, 1.0);
-                    g = c.d[m] - c.d[l] + c.e[l] / (g + (g >= 0.0 ? r : -r));
-                    double s = 1.0, cc = 1.0, p = 0.0;
-                    bool early = false;
-                    int nr = 0;
-                    for (int i = m - 1; i >= l; --i) {
-                        const double f = s * c.e[i], b = cc * c.e[i];
-                        r = hypot(f, g);
-                        c.e[i + 1] = r;
-                        if (r == 0.0) {
-                            c.d[i + 1] -= p;
-                            c.e[m] = 0.0;
-                            early = true;
-                            break;
-                        }
-                        s = f / r;
-                        cc = g / r;
-                        g = c.d[i + 1] - p;
-                        r = (c.d[i] - g) * s + 2.0 * cc * b;
-                        p = s * r;
-                        c.d[i + 1] = g + p;
-                        g = cc * r - b;
-                        c.rc[nr] = cc;
-                        c.rs[nr] = s;
-                        c.ri[nr] = i;
-                        ++nr;
-                    }
-                    if (!early) {
-                        c.d[l] -= p;
-                        c.e[l] = g;
-                        c.e[m] = 0.0;
-                    }
-                    c.nrot = nr;
-                }
-            }
-            __syncthreads();
-            const int nr = c.nrot;
-            if (nr < 0) break;
-            // eigenvector rows i, i+1 of every rotation, in order; thread per component
-            for (int q = threadIdx.x; q < n; q += EIG_THREADS) {
-                for (int t = 0; t < nr; ++t) {
-                    const int i = c.ri[t];
-                    const double co = c.rc[t], si = c.rs[t];
-                    double* a = Vt + (int64_t)i * n + q;
-                    double* b = Vt + (int64_t)(i + 1) * n + q;
-                    const double vi = *a, vj = *b;
-                    *b = si * vi + co * vj;
-                    *a = co * vi - si * vj;
-                }
-            }
+// Sturm count: eigenvalues of the tridiagonal (d, e2 = e^2) below x, from the
+// sign changes of p_i = (d_i - x) p_{i-1} - e2_{i-1} p_{i-2} (no divisions).
+// A ratio q_i = p_i / p_{i-1} of magnitude below pivmin is taken as -pivmin,
+// and the pair (p_{i-1}, p_i) is rescaled by powers of two to stay in range.
+__device__ __forceinline__ int sturm_count(int n, const double* d, const double* e2, double x, double pivmin) {
+    double a = 1.0, b = d[0] - x;
+    if (fabs(b) < pivmin) b = -pivmin;
+    int cnt = b < 0.0;
+    for (int i = 1; i < n; ++i) {
+        double c = fma(d[i] - x, b, -e2[i - 1] * a);
+        if (fabs(c) < pivmin * fabs(b)) c = -pivmin * b;
+        cnt += (c < 0.0) != (b < 0.0);
+        a = b;
+        b = c;
+        const double m = fmax(fabs(a), fabs(b));
+        if (m > 0x1p+400) {
+            a *= 0x1p-400;
+            b *= 0x1p-400;
+        } else if (m < 0x1p-400) {
+            a *= 0x1p+400;
+            b *= 0x1p+400;
+        }
+    }
+    return cnt;
+}
+
+// Eigenvector of T for the eigenvalue lam from the twisted factorisation
+// T - lam I = L+ D+ L+^T (top down) = U- D- U-^T (bottom up), twisted at r:
+// gamma_r = D+_r + D-_r - (d_r - lam); z_r = 1, z_i = -L+_i z_{i+1} above r,
+// z_{i+1} = -U-_i z_i below it, at the twist of smallest |gamma_r|.  Lp and Um
+// hold the thread's multipliers at stride ld; z (n values, contiguous)
+// receives the unit vector.  Returns false when the vector is not finite.
+__device__ bool twisted_vector(int n, const double* d, const double* e, double lam, double pivmin, double* Lp,
+                               double* Um, int64_t ld, double* z) {
+    if (n == 1) {
+        z[0] = 1.0;
+        return true;
+    }
+    double Dp = d[0] - lam;
+    for (int i = 0; i + 1 < n; ++i) {
+        if (fabs(Dp) < pivmin) Dp = Dp < 0.0 ? -pivmin : pivmin;
+        const double l = e[i] / Dp;
+        Lp[i * ld] = l;
+        Dp = (d[i + 1] - lam) - e[i] * l;
+    }
+    double best = INFINITY;
+    int r = n - 1;
+    double Dm = d[n - 1] - lam;
+    for (int t = n - 1; t >= 0; --t) {
+        if (t < n - 1) {
+            if (fabs(Dm) < pivmin) Dm = Dm < 0.0 ? -pivmin : pivmin;
+            const double u = e[t] / Dm;
+            Um[t * ld] = u;
+            Dm = (d[t] - lam) - e[t] * u;
+        }
+        const double g = fabs(t > 0 ? Dm - e[t - 1] * Lp[(t - 1) * ld] : Dm);
+        if (g < best) {
+            best = g;
+            r = t;
+        }
+    }
+    z[r] = 1.0;
+    double ss = 1.0;
+    for (int i = r - 1; i >= 0; --i) {
+        z[i] = -Lp[i * ld] * z[i + 1];
+        ss = fma(z[i], z[i], ss);
+    }
+    for (int i = r; i + 1 < n; ++i) {
+        z[i + 1] = -Um[i * ld] * z[i];
+        ss = fma(z[i + 1], z[i + 1], ss);
+    }
+    if (!(ss < INFINITY)) return false;
+    const double inv = 1.0 / sqrt(ss);
+    for (int i = 0; i < n; ++i) z[i] *= inv;
+    return true;
+}
+
+// y <- (T - sigma I)^-1 y by Gaussian elimination with partial pivoting (one
+// thread): u0, u1, u2 receive the rows of U; a zero pivot becomes `tiny`.
+__device__ void tridiagonal_solve(int n, const double* d, const double* e, double sigma, double tiny, double* y,
+                                  double* u0, double* u1, double* u2) {
+    double a = d[0] - sigma, b = n > 1 ? e[0] : 0.0, c = 0.0;  // pivot row at columns i, i+1, i+2
+    for (int i = 0; i + 1 < n; ++i) {
+        double a2 = e[i], b2 = d[i + 1] - sigma, c2 = i + 2 < n ? e[i + 1] : 0.0;
+        double yi = y[i], yn = y[i + 1];
+        if (fabs(a2) > fabs(a)) {
+            double t = a; a = a2; a2 = t;
+            t = b; b = b2; b2 = t;
+            t = c; c = c2; c2 = t;
+            t = yi; yi = yn; yn = t;
+        }
+        if (a == 0.0) a = tiny;
+        const double m = a2 / a;
+        u0[i] = a;
+        u1[i] = b;
+        u2[i] = c;
+        y[i] = yi;
+        a = b2 - m * b;
+        b = c2 - m * c;
+        c = 0.0;
+        y[i + 1] = yn - m * yi;
+    }
+    if (a == 0.0) a = tiny;
+    u0[n - 1] = a;
+    y[n - 1] /= u0[n - 1];
+    if (n >= 2) y[n - 2] = (y[n - 2] - u1[n - 2] * y[n - 1]) / u0[n - 2];
+    for (int i = n - 3; i >= 0; --i) y[i] = (y[i] - u1[i] * y[i + 1] - u2[i] * y[i + 2]) / u0[i];
+}
+
+// zk <- zk minus its components along the unit rows k0..k-1 of Z (twice),
+// normalised; returns |zk| before normalisation (block-uniform)
+__device__ double orthonormalise(int n, double* Z, int k0, int k, double* red) {
+    double* zk = Z + (int64_t)k * n;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int j = k0; j < k; ++j) {
+            const double* zj = Z + (int64_t)j * n;
+            double p = 0.0;
+            for (int i = threadIdx.x; i < n; i += EIG_THREADS) p = fma(zk[i], zj[i], p);
+            p = block_sum(p, red);
+            for (int i = threadIdx.x; i < n; i += EIG_THREADS) zk[i] = fma(-p, zj[i], zk[i]);
             __syncthreads();
         }
-        if (c.fail) return false;
     }
-    return true;
+    double q = 0.0;
+    for (int i = threadIdx.x; i < n; i += EIG_THREADS) q = fma(zk[i], zk[i], q);
+    q = sqrt(block_sum(q, red));
+    if (q > 0.0 && q < INFINITY) {
+        const double inv = 1.0 / q;
+        for (int i = threadIdx.x; i < n; i += EIG_THREADS) zk[i] *= inv;
+    }
+    __syncthreads();
+    return q;
+}
+
+// Eigenpairs of the tridiagonal T (c.s.d, c.s.e): eigenvalues ascending into
+// c.s.w, eigenvectors as the rows of Z (n x n, row-major).  Lp and Um are
+// scratch of n x min(n, EIG_THREADS) doubles each.  Eigenvalues within ctol of
+// their neighbour form clusters whose vectors are orthogonalised in order.
+__device__ void tridiagonal_eigen(int n, EigCtl& c, double* Z, double* Lp, double* Um) {
+    // split T where the coupling is negligible, |e_i| <= eps (|d_i| + |d_i+1|):
+    // the blocks then decouple exactly in the recurrences below (a coupling
+    // left at rounding level would be divided by a floored pivot)
+    if (threadIdx.x == 0)
+        for (int i = 0; i + 1 < n; ++i)
+            if (fabs(c.s.e[i]) <= 0x1p-52 * (fabs(c.s.d[i]) + fabs(c.s.d[i + 1]))) c.s.e[i] = 0.0;
+    __syncthreads();
+    double* e2 = c.s.v;
+    for (int i = threadIdx.x; i < n; i += EIG_THREADS) e2[i] = i + 1 < n ? c.s.e[i] * c.s.e[i] : 0.0;
+    // Gershgorin interval of T and the pivot floor
+    double lo = INFINITY, hi = -INFINITY, m2 = 0.0;
+    for (int i = 0; i < n; ++i) {  // (uniform over the block: shared reads)
+        const double r = (i > 0 ? fabs(c.s.e[i - 1]) : 0.0) + (i + 1 < n ? fabs(c.s.e[i]) : 0.0);
+        lo = fmin(lo, c.s.d[i] - r);
+        hi = fmax(hi, c.s.d[i] + r);
+        if (i + 1 < n) m2 = fmax(m2, c.s.e[i] * c.s.e[i]);
+    }
+    __syncthreads();
+    const double tnorm = fmax(fabs(lo), fabs(hi));
+    const double pivmin = 0x1p-200 * fmax(1.0, m2);
+    const double abstol = 0x1p-52 * tnorm;
+    lo -= 2.0 * abstol * n + pivmin;
+    hi += 2.0 * abstol * n + pivmin;
+    // eigenvalue k: count(lo) <= k < count(hi)
+    for (int k = threadIdx.x; k < n; k += EIG_THREADS) {
+        double a = lo, b = hi;
+        for (int it = 0; it < 100; ++it) {
+            const double mid = 0.5 * (a + b);
+            if (!(b - a > fmax(abstol, 0x1p-52 * fmax(fabs(a), fabs(b)))) || mid <= a || mid >= b) break;
+            if (sturm_count(n, c.s.d, e2, mid, pivmin) <= k) a = mid;
+            else b = mid;
+        }
+        c.s.w[k] = 0.5 * (a + b);
+    }
+    __syncthreads();
+    // vectors: thread slot t handles k = t, t + EIG_THREADS, ... (the twisted
+    // vector of its own eigenvalue)
+    const int nact = n < EIG_THREADS ? n : EIG_THREADS;
+    for (int k = threadIdx.x; k < n; k += EIG_THREADS)
+        if (!twisted_vector(n, c.s.d, c.s.e, c.s.w[k], pivmin, Lp + threadIdx.x, Um + threadIdx.x, nact,
+                            Z + (int64_t)k * n))
+            c.fail = 1;
+    __syncthreads();
+    // runs of equal eigenvalues (gaps <= dtol): the twisted vectors of the
+    // members after the first need not be independent, so each is replaced by
+    // three steps of inverse iteration at its eigenvalue from a pseudo-random
+    // start, orthogonalised against the earlier members after every step
+    const double ctol = 0x1p-12 * tnorm, dtol = 0x1p-44 * tnorm;
+    for (int k = 1; k < n; ++k) {
+        if (!(c.s.w[k] - c.s.w[k - 1] <= dtol)) continue;  // (uniform: shared reads)
+        int k0 = k - 1;
+        while (k0 > 0 && c.s.w[k0] - c.s.w[k0 - 1] <= dtol) --k0;
+        double* zk = Z + (int64_t)k * n;
+        for (int i = threadIdx.x; i < n; i += EIG_THREADS) {
+            const uint32_t h = (uint32_t)(i + 1) * 2654435761u ^ (uint32_t)(k + 1) * 40503u;
+            zk[i] = (double)(h >> 8) * 0x1p-23 - 1.0;
+        }
+        __syncthreads();
+        for (int it = 0; it < 3; ++it) {
+            if (threadIdx.x == 0)
+                tridiagonal_solve(n, c.s.d, c.s.e, c.s.w[k], 0x1p-52 * fmax(tnorm, pivmin), zk, Lp, Lp + n, Um);
+            __syncthreads();
+            const double q = orthonormalise(n, Z, k0, k, c.red);
+            if (!(q > 0.0 && q < INFINITY)) {
+                if (threadIdx.x == 0) c.fail = 1;
+                break;
+            }
+        }
+    }
+    // neighbours within ctol: Gram-Schmidt of each against the earlier ones
+    // (the vectors' own error is ~eps |T| / gap)
+    for (int k = 1; k < n; ++k) {
+        if (!(c.s.w[k] - c.s.w[k - 1] <= ctol)) continue;  // (uniform)
+        int k0 = k - 1;
+        while (k0 > 0 && c.s.w[k0] - c.s.w[k0 - 1] <= ctol) --k0;
+        if (!(orthonormalise(n, Z, k0, k, c.red) > 0.5) && threadIdx.x == 0) c.fail = 1;
+        __syncthreads();
+    }
 }
 
 // Fermi occupation and 1 - f without cancellation, x = beta (e - mu)
@@ -296,16 +466,31 @@ __device__ __forceinline__ double occ_weight(double x) {
 }
 
 // Divided difference of the Fermi function, times beta: (f(x_k) - f(x_l)) /
-// (e_k - e_l).  Direct quotient when the arguments are apart; otherwise the
-// central Taylor form f'(m) + f'''(m) dx^2 / 24 with f' = -g/4, f''' =
+// (e_k - e_l), given fk = f(x_k) and fl = f(x_l).  Direct quotient when the
+// arguments are apart; otherwise the central Taylor form f'(m) + f'''(m) dx^2 / 24 with f' = -g/4, f''' =
 // -(g/8) (3 t^2 - 1), g = sech^2(m/2), t = tanh(m/2) (error O(dx^4)).
-__device__ __forceinline__ double fermi_dd(double xk, double xl, double beta) {
+__device__ __forceinline__ double fermi_dd(double xk, double xl, double fk, double fl, double beta) {
     const double dx = xk - xl;
-    if (fabs(dx) > 1e-4) return beta * (occ(xk) - occ(xl)) / dx;
+    if (fabs(dx) > 1e-4) return beta * (fk - fl) / dx;
     const double m = 0.5 * (xk + xl);
     const double g = 4.0 * occ_weight(m);
     const double t = tanh(0.5 * m);
     return -0.25 * beta * g * (1.0 + (3.0 * t * t - 1.0) * dx * dx / 48.0);
+}
+
+// The subgraph i of work item j and the offset of its eigenvectors (list
+// mode or every subgraph); false past the end.
+__device__ __forceinline__ bool eig_item(const EigArgs& ea, int32_t j, int32_t& i, int64_t& voff) {
+    if (ea.list) {
+        if (j >= ea.list_n) return false;
+        i = ea.list[ea.list_base + j];
+        voff = (int64_t)j * ea.vt_stride;
+    } else {
+        if (j >= ea.a.n_sub) return false;
+        i = j;
+        voff = ea.a.moff[i];
+    }
+    return true;
 }
 
 }  // namespace
@@ -320,20 +505,27 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(EigArgs ea) {
         __syncthreads();
         if (threadIdx.x == 0) c.item = atomicAdd(ea.counter, 1);
         __syncthreads();
-        const int32_t i = c.item;
-        if (i >= a.n_sub) break;
+        int32_t i;
+        int64_t voff;
+        if (!eig_item(ea, c.item, i, voff)) break;
         const int64_t s0 = a.sub_ptr[i];
         const int n = (int)(a.sub_ptr[i + 1] - s0);
         double* A = ea.scratch + (int64_t)blockIdx.x * ea.scratch_stride;
-        double* Vt = ea.vt + a.moff[i];
+        double* Vt = ea.vt + voff;
+        double* Um = A + (int64_t)n * n;      // twisted multipliers; then Q^T
+        double* Z = Um + (int64_t)n * n;      // eigenvectors of T (rows)
         gather_dense(n, a.sub_idx + s0, a.Hptr, a.Hidx, a.Hval, A);
         tridiagonalize(n, A, c);
-        accumulate_q(n, A, Vt, c);
-        if (!ql_implicit(n, Vt, c)) {
+        tridiagonal_eigen(n, c, Z, Vt, Um);  // (Vt's storage holds L+ meanwhile)
+        if (c.fail) {
             if (threadIdx.x == 0) set_error(a.err, GB_ERR_NO_CONVERGE);
             c.fail = 0;
         }
-        // eigenvalues and the core weights sum_{j in core} V_jk^2
+        for (int k = threadIdx.x; k < n; k += EIG_THREADS) ea.eps[s0 + k] = c.s.w[k];
+        accumulate_q(n, A, Um, c);           // Q^T
+        __syncthreads();
+        gemm_nn(n, Z, Um, Vt, c.t);           // Vt = Z Q^T: row k = (Q z_k)^T
+        // the core weights sum_{j in core} V_jk^2
         const int64_t c0 = a.core_ptr[i], c1 = a.core_ptr[i + 1];
         for (int k = threadIdx.x; k < n; k += EIG_THREADS) {
             double wk = 0.0;
@@ -341,10 +533,9 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(EigArgs ea) {
                 const double x = Vt[(int64_t)k * n + a.core_pos[e]];
                 wk = fma(x, x, wk);
             }
-            ea.eps[s0 + k] = c.d[k];
             ea.w[s0 + k] = wk;
         }
-        if (threadIdx.x == 0) a.steps_out[i] = 0;
+        if (threadIdx.x == 0 && !ea.list) a.steps_out[i] = 0;
     }
 }
 
@@ -431,21 +622,33 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eig_response(EigArgs ea) {
         __syncthreads();
         if (threadIdx.x == 0) item = atomicAdd(ea.counter, 1);
         __syncthreads();
-        const int32_t i = item;
-        if (i >= a.n_sub) break;
+        int32_t i;
+        int64_t voff;
+        if (!eig_item(ea, item, i, voff)) break;
         const int64_t s0 = a.sub_ptr[i];
         const int n = (int)(a.sub_ptr[i + 1] - s0);
         const int32_t* S = a.sub_idx + s0;
-        const double* Vt = ea.vt + a.moff[i];
-        double* M = ea.scratch + (int64_t)blockIdx.x * ea.scratch_stride;  // h1, then F o h1'
-        double* T = M + (int64_t)n * n;
+        const double* Vt = ea.vt + voff;
+        double* M = ea.scratch + (int64_t)blockIdx.x * ea.scratch_stride;  // V^T h1 V, then F o (V^T h1 V)
+        double* T = M + (int64_t)n * n;                                    // h1 V
         double* V = T + (int64_t)n * n;                                    // V = Vt^T
+        double td = 0.0, tdd = 0.0;
         for (int k = threadIdx.x; k < n; k += EIG_THREADS) {
             const double x = a.beta * (ea.eps[s0 + k] - a.mu);
             fk[k] = occ(x);
             gk[k] = a.beta * occ_weight(x);
+            td = fma(fk[k], ea.w[s0 + k], td);
+            tdd = fma(occ_weight(x), ea.w[s0 + k], tdd);
         }
-        __syncthreads();
+        // the core traces at a.mu (as k_eig_traces writes them)
+        td = block_sum(td, red);
+        tdd = block_sum(tdd, red);
+        if (threadIdx.x == 0) {
+            double* tr = a.tr + (int64_t)i * a.tr_stride;
+            tr[TR_D] = td;
+            tr[TR_DD] = tdd;
+            tr[TR_D1MU] = a.beta * tdd;
+        }
         const int64_t c0 = a.core_ptr[i], c1 = a.core_ptr[i + 1];
         // d and d1_mu core columns: d[r][c] = sum_k Vt[k][r] f_k Vt[k][c]
         for (int64_t e = c0; e < c1; ++e) {
@@ -468,12 +671,12 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eig_response(EigArgs ea) {
             __syncthreads();
         }
         for (int rr = 0; rr < a.m; ++rr) {
-            gather_dense(n, S, a.H1ptr[rr], a.H1idx[rr], a.H1val[rr], M);
-            gemm_nn(n, Vt, M, T, tile);  // T = V^T h1
-            gemm_nn(n, T, V, M, tile);   // M = V^T h1 V
+            sparse_times(n, S, a.H1ptr[rr], a.H1idx[rr], a.H1val[rr], V, T);  // T = h1 V
+            gemm_nn(n, Vt, T, M, tile);                                     // M = V^T h1 V
             for (int64_t q = threadIdx.x; q < (int64_t)n * n; q += EIG_THREADS) {
                 const int k = (int)(q / n), l = (int)(q % n);
-                M[q] *= fermi_dd(a.beta * (ea.eps[s0 + k] - a.mu), a.beta * (ea.eps[s0 + l] - a.mu), a.beta);
+                M[q] *= fermi_dd(a.beta * (ea.eps[s0 + k] - a.mu), a.beta * (ea.eps[s0 + l] - a.mu), fk[k], fk[l],
+                                 a.beta);
             }
             __syncthreads();
             double tl = 0.0;
@@ -508,7 +711,10 @@ int launch_eigen(gb_handle* h, const EigArgs& ea, int which) {
     int sms = 0;
     GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     int grid = 4 * sms;
-    if (grid > ea.a.n_sub) grid = ea.a.n_sub;
+    const int32_t items = ea.list ? ea.list_n : ea.a.n_sub;
+    if (ea.list && which == 1) return GB_ERR_ARG;
+    if (items <= 0) return GB_OK;
+    if (grid > items) grid = items;
     if (which == 0) {
         if (grid > GB_EIG_MAX_CTAS) grid = GB_EIG_MAX_CTAS;
         GB_CUDA(cudaMemsetAsync(ea.counter, 0, sizeof(int32_t), h->stream));
@@ -538,7 +744,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eig_jacobian(EigArgs ea, Precon
     const PassArgs& a = ea.a;
     __shared__ Tile tile;
     __shared__ double red[EIG_THREADS / 32];
-    __shared__ double gk[GB_EIG_MAX_N], uv[GB_EIG_MAX_N];
+    __shared__ double gk[GB_EIG_MAX_N], fk[GB_EIG_MAX_N], uv[GB_EIG_MAX_N];
     __shared__ int32_t catom[GB_PRECOND_MAX_ATOMS];
     __shared__ int item;
     for (;;) {
@@ -562,8 +768,10 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eig_jacobian(EigArgs ea, Precon
         const int na = (int)(pa.atom_ptr[i + 1] - a0);
         const int64_t c0 = a.core_ptr[i], c1 = a.core_ptr[i + 1];
         for (int b = threadIdx.x; b < na; b += EIG_THREADS) catom[b] = pa.atoms[a0 + b];
-        for (int k = threadIdx.x; k < n; k += EIG_THREADS)
+        for (int k = threadIdx.x; k < n; k += EIG_THREADS) {
             gk[k] = a.beta * occ_weight(a.beta * (ea.eps[s0 + k] - a.mu));
+            fk[k] = occ(a.beta * (ea.eps[s0 + k] - a.mu));
+        }
         for (int64_t q = threadIdx.x; q < (int64_t)n * n; q += EIG_THREADS) V[q] = Vt[(q % n) * n + q / n];
         for (int q = threadIdx.x; q < na * na; q += EIG_THREADS) chi[q] = 0.0;
         __syncthreads();
@@ -599,7 +807,8 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eig_jacobian(EigArgs ea, Precon
             gemm_nn(n, T, V, M, tile);
             for (int64_t q = threadIdx.x; q < (int64_t)n * n; q += EIG_THREADS) {
                 const int k = (int)(q / n), l = (int)(q % n);
-                M[q] *= fermi_dd(a.beta * (ea.eps[s0 + k] - a.mu), a.beta * (ea.eps[s0 + l] - a.mu), a.beta);
+                M[q] *= fermi_dd(a.beta * (ea.eps[s0 + k] - a.mu), a.beta * (ea.eps[s0 + l] - a.mu), fk[k], fk[l],
+                                 a.beta);
             }
             __syncthreads();
             // d1_lambda_pp = u_p^T (F o h1') u_p for every core orbital p, u_p[k] = Vt[k][p]

@@ -60,7 +60,7 @@ def test_eigen_single_subgraph_equals_full(gb):
 
 def test_eigen_degenerate_and_tiny(gb):
     # exact degeneracies (a block-diagonal H with repeated blocks) and 1-, 2-,
-    # 3-orbital subgraphs: the QL iteration and the divided differences
+    # 3-orbital subgraphs: the bisection, the twists and the divided differences
     blocks = [np.array([[-1.0]]), np.array([[-2.0, 0.5], [0.5, -2.0]]),
               np.array([[0.0, 1.0, 0.0], [1.0, 0.0, 1.0], [0.0, 1.0, 0.0]])]
     A = np.zeros((18, 18))
@@ -83,6 +83,42 @@ def test_eigen_degenerate_and_tiny(gb):
     P = gb.partition(gb.graph_build(Hd, 0.0), torch.as_tensor(groups))
     R = gb.density_and_response(Hd, [to_device(H1c)], 0.2, 14.0, P, precision="eigen")
     eD, eD1 = max_abs_block_error(R, ref, part)
+    assert eD <= 1e-9 and eD1 <= 1e-9
+
+
+def test_eigen_degenerate_inside_one_subgraph(gb):
+    # one subgraph holding repeated blocks and isolated orbitals of equal
+    # energy, coupled at rounding level (as decoupled p orbitals appear in a
+    # water subgraph): runs of equal eigenvalues inside one tridiagonal matrix,
+    # split where the coupling is negligible, each member on its own twist
+    rng = np.random.default_rng(7)
+    chain = np.array([[-3.0, 1.0, 0.0], [1.0, -2.5, 0.7], [0.0, 0.7, -1.0]])
+    pair = np.array([[-9.0, 0.4], [0.4, -8.5]])
+    blocks = [chain, pair, chain, np.array([[-9.3]]), pair, np.array([[-9.3]]), chain,
+              np.array([[-9.3]]), np.array([[-9.3]])]
+    n = sum(b.shape[0] for b in blocks)
+    A = np.zeros((n, n))
+    o = 0
+    for b in blocks:
+        k = b.shape[0]
+        A[o:o + k, o:o + k] = b
+        o += k
+    # rounding-level couplings between the blocks
+    for _ in range(12):
+        i, j = rng.integers(0, n, 2)
+        if i != j:
+            A[i, j] = A[j, i] = 1e-16 * rng.normal()
+    from synth import CSR
+    Hc = CSR.from_dense(A)
+    H1c = CSR.from_dense(np.diag(np.linspace(-0.3, 0.2, n)))
+    # 4 occupied: mu at the four-fold -9.3 level, which is half filled
+    full = oracle_full(A, [np.diag(np.linspace(-0.3, 0.2, n))], 0.2, 4.0)
+    Hd = to_device(Hc)
+    P = gb.partition(gb.graph_build(Hd, 0.0), torch.zeros(n, dtype=torch.int32))
+    R = gb.density_and_response(Hd, [to_device(H1c)], 0.2, 8.0, P, precision="eigen")
+    eD = np.abs(dense_result(R.D) - full.D).max()
+    eD1 = np.abs(dense_result(R.D, R.D1[0].val) - full.D1[0]).max()
+    print(f"eigen degenerate runs in one subgraph (n={n}): max|dD|={eD:.2e} max|dD1|={eD1:.2e}")
     assert eD <= 1e-9 and eD1 <= 1e-9
 
 
