@@ -199,6 +199,11 @@ int64_t gb_launch_count(const gb_handle* h);
 /* Human-readable name of a status code (static string). */
 const char* gb_status_string(int status);
 
+/* The CUDA runtime error (cudaError_t value) behind the most recent
+ * GB_ERR_DEVICE returned by any call in this process, 0 if none; *name (if
+ * non-NULL) receives its name.  Diagnostic only: not thread-safe. */
+int gb_last_device_error(const char** name);
+
 /* Library version and the compute capability it was built for (e.g. 103). */
 int gb_version(int32_t* major, int32_t* minor, int32_t* arch);
 

@@ -19,7 +19,12 @@ PRECISION = {"fp64": 0, "fp16x3": 1, "bf16x3": 2, "eigen": 3}
 
 class GbError(RuntimeError):
     def __init__(self, func: str, status: int):
-        super().__init__(f"{func} returned {STATUS.get(status, status)}")
+        msg = f"{func} returned {STATUS.get(status, status)}"
+        if STATUS.get(status) == "GB_ERR_DEVICE" and _lib is not None:
+            name = C.c_char_p()
+            code = _lib.gb_last_device_error(C.byref(name))
+            msg += f" (CUDA error {code}: {name.value.decode() if name.value else '?'})"
+        super().__init__(msg)
         self.status = status
 
 
@@ -114,6 +119,7 @@ SIGNATURES = [
                                    C.c_void_p, C.POINTER(gb_blocks), C.c_double, C.c_int32, C.c_double,
                                    C.POINTER(gb_opts), C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+    ("gb_last_device_error", C.c_int, [C.POINTER(C.c_char_p)]),
     ("gb_plan_autotune", C.c_int, [C.c_void_p, C.POINTER(gb_csr), C.POINTER(gb_csr), C.c_int32, C.c_double,
                                    C.c_double, C.POINTER(gb_part), C.POINTER(gb_opts), C.c_double,
                                    C.POINTER(gb_csc), C.POINTER(gb_csc), C.POINTER(gb_plan)]),

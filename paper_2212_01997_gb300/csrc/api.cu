@@ -51,6 +51,15 @@ extern "C" size_t gb_required_workspace(const gb_handle* h) { return h ? h->requ
 
 extern "C" int64_t gb_launch_count(const gb_handle* h) { return h ? h->launches : 0; }
 
+static int g_last_device_error = 0;
+
+void gb_note_device_error(cudaError_t e) { g_last_device_error = (int)e; }
+
+extern "C" int gb_last_device_error(const char** name) {
+    if (name) *name = cudaGetErrorName((cudaError_t)g_last_device_error);
+    return g_last_device_error;
+}
+
 extern "C" const char* gb_status_string(int status) {
     switch (status) {
         case GB_OK: return "GB_OK";

@@ -25,10 +25,16 @@ struct gb_handle {
     gb_plan plan;
 };
 
+// the CUDA error behind the last GB_ERR_DEVICE (gb_last_device_error)
+void gb_note_device_error(cudaError_t e);
+
 #define GB_CUDA(call)                                   \
     do {                                                \
         cudaError_t e_ = (call);                        \
-        if (e_ != cudaSuccess) return GB_ERR_DEVICE;    \
+        if (e_ != cudaSuccess) {                        \
+            gb_note_device_error(e_);                   \
+            return GB_ERR_DEVICE;                       \
+        }                                               \
     } while (0)
 
 #define GB_TRY(call)                   \
@@ -46,7 +52,10 @@ struct gb_handle {
         kernel<<<(grid), (block), (smem), (st)>>>(__VA_ARGS__);                       \
         (h)->launches++;                                                              \
         cudaError_t e_ = cudaGetLastError();                                          \
-        if (e_ != cudaSuccess) return GB_ERR_DEVICE;                                  \
+        if (e_ != cudaSuccess) {                                                      \
+            gb_note_device_error(e_);                                                 \
+            return GB_ERR_DEVICE;                                                     \
+        }                                                                             \
     } while (0)
 
 // Bump allocator over the caller's workspace.  With base == nullptr it only
