@@ -872,7 +872,12 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
     // The tiled class runs beside the one-tile classes on a second stream when
     // it holds few subgraphs (one per SM taken from the others' grid), after
     // them when it holds many (then it fills the GPU by itself).
+    // When it runs beside them, a second launch of the 128-column kernel
+    // follows it on its stream: big_grid more CTAs that draw on the same work
+    // counter, so the SMs the tiled class held join the one-tile class once
+    // it is done (their response scratch follows the first launch's).
     bool concurrent = false;
+    int64_t tail_cta0 = -1;
     if (big) {
         int sms = 0;
         GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
@@ -880,6 +885,8 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
         concurrent = big_grid > 0 && 4 * big_grid <= sms && nclass[0] + nclass[1] > 0;
         if (concurrent) {
             a.grid_sms = sms - big_grid;
+            const int64_t z1_ctas = n_sub < GB_SPLIT_MAX_CTAS ? n_sub : GB_SPLIT_MAX_CTAS;
+            if (o.split_small_npad <= 0 && sms <= z1_ctas) tail_cta0 = a.grid_sms;
             if (!h->aux) GB_CUDA(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
             if (!h->ev_fork) GB_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
             if (!h->ev_join) GB_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
@@ -942,6 +949,12 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
                 GB_CUDA(cudaEventRecord(h->ev_fork, st));
                 GB_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
                 GB_TRY(launch_split_pass_big(h, bb, big_grid, h->aux));
+                if (tail_cta0 >= 0) {
+                    PassArgs t = a;
+                    t.grid_sms = big_grid;
+                    t.z1pool = a.z1pool + tail_cta0 * (m > 0 ? m : 1) * GB_SPLIT_MAX_N * GB_SPLIT_MAX_N;
+                    GB_TRY(launch_split_pass_on(h, t, h->aux));
+                }
                 GB_CUDA(cudaEventRecord(h->ev_join, h->aux));
             }
             // the 128-column class: its list when the small class is in use,

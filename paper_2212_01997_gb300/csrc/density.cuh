@@ -135,6 +135,8 @@ __device__ __forceinline__ int recursion_steps(double beta, double mu, double lo
 }
 
 int launch_split_pass(gb_handle* h, const PassArgs& a);
+// the same launch on another stream (a.grid_sms SMs)
+int launch_split_pass_on(gb_handle* h, const PassArgs& a, cudaStream_t stream);
 // the same recursion over a list of subgraphs (a.work): the 128-column
 // configuration, and the small one for round16(|S_i|) <= 64 (two CTAs per SM)
 int launch_split_pass_listed(gb_handle* h, const PassArgs& a);

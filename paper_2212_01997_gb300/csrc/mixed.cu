@@ -1161,7 +1161,7 @@ int launch_split_gather(gb_handle* h, const PassArgs& a, float* hblk, double* hd
 
 #endif
 
-int GB_SPLIT_LAUNCH(gb_handle* h, const PassArgs& a) {
+static int split_launch(gb_handle* h, const PassArgs& a, cudaStream_t stream) {
     static bool configured = false;
     if (!configured) {
         GB_CUDA(cudaFuncSetAttribute(GB_SPLIT_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
@@ -1176,6 +1176,14 @@ int GB_SPLIT_LAUNCH(gb_handle* h, const PassArgs& a) {
     int64_t grid = (int64_t)GB_SPLIT_MINB * sms;
     if (grid > a.n_sub) grid = a.n_sub;
     if (grid > cap) grid = cap;
-    GB_LAUNCH(h, GB_SPLIT_KERNEL, (int)grid, THREADS, SMEM_BYTES, a);
+    GB_LAUNCH_ON(h, stream, GB_SPLIT_KERNEL, (int)grid, THREADS, SMEM_BYTES, a);
     return GB_OK;
 }
+
+int GB_SPLIT_LAUNCH(gb_handle* h, const PassArgs& a) { return split_launch(h, a, h->stream); }
+
+#if GB_SPLIT_NPMAX == 128 && !GB_SPLIT_LIST
+int launch_split_pass_on(gb_handle* h, const PassArgs& a, cudaStream_t stream) {
+    return split_launch(h, a, stream);
+}
+#endif

@@ -475,3 +475,27 @@ def test_split_water4k_six_rhs(gb):
     print(f"water4k m=6 kT=0.1: max|dD|={eD:.2e} max|dD1|={eD1:.2e} dmu={R.mu - ref.mu:.2e} "
           f"passes={R.report['passes']}")
     assert eD <= TOL["fp16x3"] and eD1 <= TOL["fp16x3"]
+
+
+def test_split_tiled_class_beside_one_tile(gb):
+    # a few large subgraphs among many small ones: the tiled kernel runs on
+    # its own stream beside the 128-column kernel, and a second launch of the
+    # 128-column kernel behind it takes over its SMs (same work counter)
+    wl, system, h1 = make_workload("water1k", n_rhs=1)
+    H = system.H
+    groups = np.asarray(system.orb_group, dtype=np.int32).copy()
+    for k in range(6):  # molecules 3k .. 3k+2 share one core: subgraphs above 128
+        groups[np.isin(groups, [3 * k + 1, 3 * k + 2])] = 3 * k
+    groups = np.unique(groups, return_inverse=True)[1].astype(np.int32)
+    part = o_part(o_graph(H.n, H.indptr, H.indices, H.data, wl.tau), groups)
+    npads = (part.sizes() + 15) // 16 * 16
+    assert 0 < (npads > 128).sum() <= 8 and (npads <= 128).sum() > 900
+    ref = oracle_graph(H, h1, wl.kT, system.n_occ, part, workers=8)
+    Hd = to_device(H)
+    P = gb.partition(gb.graph_build(Hd, wl.tau), torch.as_tensor(groups))
+    R = gb.density_and_response(Hd, [to_device(h1[0])], wl.kT, system.n_electrons, P, precision="fp16x3",
+                                mu0=ref.mu)
+    eD, eD1 = max_abs_block_error(R, ref, part)
+    print(f"tiled beside one-tile: {(npads > 128).sum()} tiled of {len(npads)}; max|dD|={eD:.2e} "
+          f"max|dD1|={eD1:.2e} dmu={R.mu - ref.mu:.2e}")
+    assert eD <= TOL["fp16x3"] and eD1 <= TOL["fp16x3"]
