@@ -533,24 +533,34 @@ def run_trajectory(args, rank, world):
                 R.D.val.to("cpu", non_blocking=True)] + [d.val.to("cpu", non_blocking=True) for d in R.D1])
         return P, R, out
 
-    mu = math.nan
+    # the starting mu of a step: the previous geometry's mu, extrapolated
+    # linearly from the two before it when they are consecutive geometries
+    hist = []
+
+    def mu_start(g):
+        if len(hist) >= 2 and hist[-1][0] == g - 1 and hist[-2][0] == g - 2:
+            return 2.0 * hist[-1][1] - hist[-2][1]
+        return hist[-1][1] if hist else math.nan
+
     for g in range(max(args.warmup, 3)):
-        _, R, _ = step(g, "fp16x3", mu)
-        mu = R.mu
+        _, R, _ = step(g, "fp16x3", mu_start(g))
+        hist.append((g, R.mu))
     clocks = ClockSampler(0)
     clocks.start()
-    ms, bo, redo_n, redo_ms = [], 0, [], []
+    ms, bo, redo_n, redo_ms, passes = [], 0, [], [], []
     for k in range(steps):
         flush.zero_()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        P, R, out = step(k, "fp16x3", mu)
+        P, R, out = step(k, "fp16x3", mu_start(k))
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms.append(e0.elapsed_time(e1))
         redo_n.append(R.report["refined"])
         redo_ms.append(R.report["refine_ms"])
+        passes.append(R.report["passes"])
+        hist.append((k, R.mu))
         mu, bo = R.mu, sum(t.numel() * t.element_size() for t in out)
     clk = clocks.stop()
     # the FP64 path on the last geometry, and both at its mu
@@ -588,7 +598,8 @@ def run_trajectory(args, rank, world):
             "h2d_bytes_per_step": statistics.mean(bi), "d2h_bytes_per_step": bo,
             "fp64_path": {"seconds_per_step": s64, "steps_per_s": 1.0 / s64, "passes": R64.report["passes"]},
             "mixed_over_fp64": s64 / (statistics.mean(ms) / 1e3), "accuracy_vs_fp64_gpu": acc,
-            "clocks": clk, "passes_last": R.report["passes"],
+            "clocks": clk, "passes_last": R.report["passes"], "passes_mean": statistics.mean(passes),
+            "mu_start": "previous geometry's mu, extrapolated linearly from the two before it",
             "fp64_redo": {"threshold": args.refine_d1,
                           "rule": "subgraphs with a collected |D1| entry above the threshold recomputed in FP64 "
                                   "(eigenbasis) at the accepted mu, inside the timed step",
