@@ -17,6 +17,7 @@
 
 #include "bitset.cuh"
 #include "common.cuh"
+#include "warpsort.cuh"
 
 namespace {
 
@@ -86,11 +87,10 @@ __global__ void k_edge_fill(int32_t n, const int64_t* ptr, const int32_t* idx, c
 }
 
 // Rows of at most SORT_EPL x 32 (duplicated) edges: a warp per row holds the
-// row in registers (SORT_EPL per lane, lane-major), sorts it with a bitonic
-// network (compare-exchange inside a lane's registers below SORT_EPL, across
-// lanes by shuffles above), and writes each distinct value once, ascending,
-// over the front of the row's own edge list (all reads precede the writes).
-// Longer rows are left to k_row_unique.
+// row in registers (SORT_EPL per lane), sorts it (warp_bitonic_sort) and
+// writes each distinct value once, ascending, over the front of the row's own
+// edge list (all reads precede the writes).  Longer rows are left to
+// k_row_unique.
 constexpr int SORT_EPL = 16;
 constexpr int SORT_MAX = 32 * SORT_EPL;
 
@@ -104,52 +104,14 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_unique_warp(int32_t n, cons
         if (len > SORT_MAX) continue;
         int32_t v[SORT_EPL];
 #pragma unroll
-        for (int k = 0; k < SORT_EPL; ++k) {
-            const int e = lane * SORT_EPL + k;
+        for (int k = 0; k < SORT_EPL; ++k) {  // (any arrangement: the set is what is sorted)
+            const int e = k * 32 + lane;
             v[k] = e < len ? edges[a + e] : INT32_MAX;
         }
-#pragma unroll
-        for (int size = 2; size <= SORT_MAX; size <<= 1) {
-#pragma unroll
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                if (stride >= SORT_EPL) {
-                    const int lx = stride / SORT_EPL;
-#pragma unroll
-                    for (int k = 0; k < SORT_EPL; ++k) {
-                        const int e = lane * SORT_EPL + k;
-                        const int32_t o = __shfl_xor_sync(0xffffffffu, v[k], lx);
-                        const bool up = (e & size) == 0, low = (e & stride) == 0;
-                        v[k] = (low == up) ? min(v[k], o) : max(v[k], o);
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < SORT_EPL; ++k) {
-                        if (k & stride) continue;
-                        const int k2 = k | stride;
-                        const bool up = ((lane * SORT_EPL + k) & size) == 0;
-                        const int32_t x = v[k], y = v[k2];
-                        v[k] = up ? min(x, y) : max(x, y);
-                        v[k2] = up ? max(x, y) : min(x, y);
-                    }
-                }
-            }
-        }
-        // keep the first of each run of equal values (the padding sorts last)
-        const int32_t prev_last = __shfl_up_sync(0xffffffffu, v[SORT_EPL - 1], 1);
-        uint32_t keep = 0;
-#pragma unroll
-        for (int k = 0; k < SORT_EPL; ++k) {
-            const int32_t p = k > 0 ? v[k - 1] : (lane > 0 ? prev_last : INT32_MIN);
-            if (v[k] != INT32_MAX && v[k] != p) keep |= 1u << k;
-        }
-        const int mine = __popc(keep);
-        int before = mine;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, before, o);
-            if (lane >= o) before += t;
-        }
-        const int total = __shfl_sync(0xffffffffu, before, 31);
-        before -= mine;
+        warp_bitonic_sort<SORT_EPL>(v);
+        const uint32_t keep = warp_run_starts<SORT_EPL>(v);
+        int total;
+        int before = warp_exclusive_scan(__popc(keep), &total);
         __syncwarp();
 #pragma unroll
         for (int k = 0; k < SORT_EPL; ++k)

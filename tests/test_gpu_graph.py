@@ -130,6 +130,36 @@ def test_random_graph_blocks_and_edge_cases(gb):
     assert P.n_sub == 4 and P.max_sub == 3
 
 
+def test_warp_and_block_paths_in_one_call(gb):
+    # rows on both sides of the graph build's warp-sort limit (512 edges per
+    # row, the rest deduplicated by the block bitmap kernel: a hub vertex of
+    # degree ~900), then cores of 1 to 250 vertices (core plus neighbour
+    # lists from 9 to ~16,000 entries) in one partition, bit-exact against
+    # the oracle
+    rng = np.random.default_rng(11)
+    n = 2000
+    A = (rng.random((n, n)) < 0.004) * rng.normal(size=(n, n))
+    A[0, rng.choice(n, size=900, replace=False)] = 1.0
+    A = 0.5 * (A + A.T)
+    np.fill_diagonal(A, 1.0)
+    Ac = CSR.from_dense(A)
+    G = gb.graph_build(to_device(Ac), 0.0)
+    adj = o_graph(n, Ac.indptr, Ac.indices, Ac.data, 0.0)
+    _check_graph(G, adj)
+    assert np.diff(adj.indptr).max() > 512
+    sizes = np.concatenate([rng.integers(1, 6, size=200), [250, 180, 120]])
+    groups = np.repeat(np.arange(len(sizes)), sizes)[:n]
+    groups = np.concatenate([groups, np.full(n - len(groups), len(sizes))]).astype(np.int32)
+    groups = groups[rng.permutation(n)]
+    P = gb.partition(G, torch.as_tensor(groups), len(sizes) + 1)
+    ref = o_part(adj, groups)
+    _check_partition(P, ref)
+    deg = np.diff(adj.indptr)
+    entries = np.array([len(c) + deg[c].sum() for c in (ref.core_idx[ref.core_ptr[i]:ref.core_ptr[i + 1]]
+                                                         for i in range(len(ref.core_ptr) - 1))])
+    assert entries.min() <= 1024 < entries.max()
+
+
 def test_argument_errors(gb):
     wl, system, _ = make_workload("water64", n_rhs=0)
     H = to_device(system.H)
