@@ -29,7 +29,10 @@
 //   [left | right] += A_hi [B_hi | B_lo]   (one instruction, N = 2 NT)
 //   right          += A_lo B_hi
 // (the one-tile kernel's packing: the left accumulator holds only the large
-// A_hi B_hi terms).  Thread 0 runs a three-stage ring of 64-wide K chunks
+// A_hi B_hi terms), with left split in two accumulators by K chunk (see
+// mma_chunk: the tensor cores' FP32 accumulation rounds toward zero, and the
+// many K steps of a large subgraph would otherwise bias the products
+// toward zero).  Thread 0 runs a three-stage ring of 64-wide K chunks
 // (bulk copies completing on mbarriers, MMAs releasing the stage through
 // tcgen05.commit) and issues the MMAs; then all 8 warps (4 TMEM lane
 // quadrants x 2 column halves) run the tile's epilogue, which adds the
@@ -47,7 +50,7 @@ constexpr int NSTG = 3;                             // pipeline stages
 constexpr uint32_t A_PART = 128u * KC * 2u;         // one part of an A chunk (16 KB)
 constexpr uint32_t B_PART = (uint32_t)KC * NT * 2u; // one part of a B chunk (16 KB)
 constexpr uint32_t STG_BYTES = 2u * A_PART + 2u * B_PART;
-constexpr uint32_t TMEM_COLS = 2 * NT;              // [left | right] of one tile
+constexpr uint32_t TMEM_COLS = 4 * NT;              // [left_a | right | left_b] of one tile (3 NT used)
 constexpr float STAGE_SCALE = 4096.f;               // staged value = 2^12 x value
 constexpr float TMEM_SCALE = 16777216.f;            // FP32 state = 2^24 x value
 constexpr float TMEM_INV = 1.f / 16777216.f;
@@ -176,7 +179,9 @@ struct Big {
 
     // ---- thread 0: the K-chunk ring --------------------------------------
     // chunk q of a tile: term q / nkc, K columns [k0, k0 + kw)
-    __device__ bool load_chunk(uint32_t g, const Term& t, int mt, int n0, int N, int k0, int kw, bool hh) {
+    // (swap: the B parts land lo first, then hi, for an odd chunk; see mma_chunk)
+    __device__ bool load_chunk(uint32_t g, const Term& t, int mt, int n0, int N, int k0, int kw, bool hh,
+                               bool swap) {
         const uint32_t s = g % NSTG;
         if (g >= NSTG && !mbar_wait(smem_u32(&c.empty[s]), ((g / NSTG) - 1) & 1u)) return false;
         const uint32_t sa = stg_addr + s * STG_BYTES;
@@ -192,7 +197,8 @@ struct Big {
         for (int p = 0; p < parts; ++p) {
             bulk_copy(sa + p * A_PART, A + p * parti, abytes, fb);
             for (int gi = 0; gi < ng; ++gi)
-                bulk_copy(sb + (uint32_t)(p * ng + gi) * 1024u, B + p * parti + (int64_t)gi * 2048, bbytes, fb);
+                bulk_copy(sb + (uint32_t)(((swap ? 1 - p : p) * ng) + gi) * 1024u, B + p * parti + (int64_t)gi * 2048,
+                          bbytes, fb);
         }
         return true;
     }
@@ -204,19 +210,42 @@ struct Big {
             : "memory");
     }
 
-    __device__ void mma_chunk(uint32_t g, int N, int kw, bool hh, bool first) {
+    // The large A_hi B_hi terms go to two accumulators, even chunks to left_a
+    // (columns [0, N)) and odd chunks to left_b ([2N, 3N)), which the epilogue
+    // adds in FP32 (round to nearest): each accumulator then takes half of the
+    // K steps' round-toward-zero additions at about half the magnitude, which
+    // halves their bias.  Even chunk: [left_a | right] += A_hi [B_hi | B_lo]
+    // (B staged hi first); odd chunk: [right | left_b] += A_hi [B_lo | B_hi]
+    // (B staged lo first); then right += A_lo B_hi.  q is the chunk's index in
+    // the tile (the big kernel's tiles hold at least 3 chunks, so left_b is
+    // always written).
+    __device__ void mma_chunk(uint32_t g, int N, int kw, bool hh, int q) {
         const uint32_t s = g % NSTG;
         const uint32_t sa = stg_addr + s * STG_BYTES;
         const uint32_t sb = sa + 2 * A_PART;
         const uint32_t id1 = make_idesc(fmt, 0, N), id2 = make_idesc(fmt, 0, 2 * N);
+        const bool odd = (q & 1) != 0;
+        const uint32_t la = tbase, rt = tbase + (uint32_t)N, lb = tbase + 2u * (uint32_t)N;
+        const uint32_t hi_grp = (uint32_t)(N / 8) * 1024u;  // the hi part of a swapped B chunk
         for (int ks = 0; ks < kw / 16; ++ks) {
-            const uint32_t acc = (first && ks == 0) ? 0u : 1u;
-            const uint64_t b = desc_b(sb + (uint32_t)ks * 256u);
+            const uint64_t a_hi = desc_a(sa + (uint32_t)ks * 4096u);
+            const uint64_t a_lo = desc_a(sa + A_PART + (uint32_t)ks * 4096u);
+            const uint64_t b0 = desc_b(sb + (uint32_t)ks * 256u);
+            const bool init = q <= 1 && ks == 0;  // the first K step of left_a / left_b
             if (hh) {
-                mma_f16(tbase, desc_a(sa + (uint32_t)ks * 4096u), b, id1, acc);
+                mma_f16(odd ? lb : la, a_hi, b0, id1, init ? 0u : 1u);
+            } else if (!odd) {
+                mma_f16(la, a_hi, b0, id2, init ? 0u : 1u);
+                mma_f16(rt, a_lo, b0, id1, 1u);
             } else {
-                mma_f16(tbase, desc_a(sa + (uint32_t)ks * 4096u), b, id2, acc);
-                mma_f16(tbase + (uint32_t)N, desc_a(sa + A_PART + (uint32_t)ks * 4096u), b, id1, 1u);
+                const uint64_t b_hi = desc_b(sb + hi_grp + (uint32_t)ks * 256u);
+                if (init) {  // right accumulates, left_b starts: two instructions
+                    mma_f16(rt, a_hi, b0, id1, 1u);
+                    mma_f16(lb, a_hi, b_hi, id1, 0u);
+                } else {
+                    mma_f16(rt, a_hi, b0, id2, 1u);
+                }
+                mma_f16(rt, a_lo, b_hi, id1, 1u);
             }
         }
     }
@@ -235,7 +264,7 @@ struct Big {
         for (int q = 0; q < total && q < NSTG - 1 && ok; ++q) {
             int k0, kw;
             chunk(q, k0, kw);
-            ok = load_chunk(g0 + q, t[q / nkc], mt, n0, N, k0, kw, hh);
+            ok = load_chunk(g0 + q, t[q / nkc], mt, n0, N, k0, kw, hh, (q & 1) && !hh);
             issued += ok;
         }
         for (int q = 0; q < total && ok; ++q) {
@@ -247,12 +276,13 @@ struct Big {
                 break;
             }
             ++waited;
-            mma_chunk(g, N, kw, hh, q == 0);
+            mma_chunk(g, N, kw, hh, q);
             mma_commit(smem_u32(&c.empty[g % NSTG]));
             if (q + NSTG - 1 < total) {
                 int k1, kw1;
                 chunk(q + NSTG - 1, k1, kw1);
-                ok = load_chunk(g + NSTG - 1, t[(q + NSTG - 1) / nkc], mt, n0, N, k1, kw1, hh);
+                ok = load_chunk(g + NSTG - 1, t[(q + NSTG - 1) / nkc], mt, n0, N, k1, kw1, hh,
+                                ((q + NSTG - 1) & 1) && !hh);
                 issued += ok;
             }
         }
@@ -331,17 +361,20 @@ struct Big {
         float* FO = e.fo >= 0 ? f32(e.fo) : nullptr;
         uint8_t* SO = e.so >= 0 ? img(e.so) : nullptr;
         for (int u = grp; u < N / 8; u += 2) {
-            uint32_t r1[8], r2[8];
-            tmem_ld8_issue(tbase + lane_off + 8 * u, r1);
+            uint32_t r1[8], r2[8], r3[8];
+            tmem_ld8_issue(tbase + lane_off + 8 * u, r1);                        // left_a
+            tmem_ld8_issue(tbase + lane_off + 2 * N + 8 * u, r3);                // left_b
             if (right) tmem_ld8_issue(tbase + lane_off + N + 8 * u, r2);
             tmem_wait_ld();
             pin8(r1);
+            pin8(r3);
             if (right) pin8(r2);
             const int c0 = n0 + 8 * u;
             float v[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const float p = __uint_as_float(r1[j]) + (right ? __uint_as_float(r2[j]) : 0.f);
+                const float big = __uint_as_float(r1[j]) + __uint_as_float(r3[j]);
+                const float p = big + (right ? __uint_as_float(r2[j]) : 0.f);
                 v[j] = e.kp * p;
             }
             if (F1) {
