@@ -337,7 +337,8 @@ def measure(gb, workload, steps, warmup, fp64_steps, dev, stream, handle, world,
     t_step = max_over_ranks(statistics.mean(t_m), world, dist, dev)
     sizes = (P.sub_ptr[1:] - P.sub_ptr[:-1]).float()
     out.update(P=P, ms=t_step, value=whole_job_rate(system.n_orb, t_step, world), launches=n_launch,
-               passes=pass_m[-1], max_steps=Rm.report["max_steps"], mu=Rm.mu, mu1=Rm.mu1[0],
+               passes=pass_m[-1], passes_per_step=pass_m, max_steps=Rm.report["max_steps"], mu=Rm.mu,
+               mu1=Rm.mu1[0],
                kernel_ms=statistics.mean(k / p for k, p in zip(k_m, pass_m)),
                flops=statistics.mean(fl_m), flops_per_step_count=statistics.mean(fls_m),
                mean_sub=float(sizes.mean().item()), n_tiled=int((sizes > 128).sum().item()))
@@ -770,7 +771,8 @@ def main():
             "clocks": head["clocks"], "fp64_path": head.get("fp64"), "fp64_eigen_path": head.get("fp64_eigen"),
             "mixed_over_fp64": head["value"] / world / head["fp64"]["value"] if "fp64" in head else None,
             "accuracy_vs_fp64_gpu": head.get("accuracy_vs_fp64_gpu"),
-            "mu": head["mu"], "mu1": head["mu1"], "passes": head["passes"], "max_steps": head["max_steps"],
+            "mu": head["mu"], "mu1": head["mu1"], "passes": head["passes"],
+            "passes_per_step": head["passes_per_step"], "max_steps": head["max_steps"],
 
             "max_abs_D_minus_DT": head.get("max_abs_D_minus_DT"), "moving": head.get("moving"),
         }
@@ -778,6 +780,7 @@ def main():
             "workload": f"{c['workload']}: {workload_text(c['wl'], c['system'])}", "value": c["value"],
             "unit": "orbitals/s", "ms_per_step": c["ms"], "fp64_path": c["fp64"],
             "mixed_over_fp64": c["value"] / world / c["fp64"]["value"], "passes": c["passes"],
+            "passes_per_step": c["passes_per_step"],
             "accuracy_vs_fp64_gpu": c["accuracy_vs_fp64_gpu"], "clocks": c["clocks"],
             "max_steps": c["max_steps"], "max_subgraph": c["P"].max_sub, "subgraphs_above_128": c["n_tiled"]}
             for c in comps]
