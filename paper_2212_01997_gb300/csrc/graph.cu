@@ -17,7 +17,6 @@
 
 #include "bitset.cuh"
 #include "common.cuh"
-#include "warpsort.cuh"
 
 namespace {
 
@@ -86,52 +85,15 @@ __global__ void k_edge_fill(int32_t n, const int64_t* ptr, const int32_t* idx, c
     }
 }
 
-// Rows of at most SORT_EPL x 32 (duplicated) edges: a warp per row holds the
-// row in registers (SORT_EPL per lane), sorts it (warp_bitonic_sort) and
-// writes each distinct value once, ascending, over the front of the row's own
-// edge list (all reads precede the writes).  Longer rows are left to
-// k_row_unique.
-constexpr int SORT_EPL = 16;
-constexpr int SORT_MAX = 32 * SORT_EPL;
-
-__global__ void __launch_bounds__(ROW_THREADS) k_row_unique_warp(int32_t n, const int64_t* off, int32_t* edges,
-                                                                 int64_t* count) {
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = w0; i < n; i += nw) {
-        const int64_t a = off[i], len = off[i + 1] - a;
-        if (len > SORT_MAX) continue;
-        int32_t v[SORT_EPL];
-#pragma unroll
-        for (int k = 0; k < SORT_EPL; ++k) {  // (any arrangement: the set is what is sorted)
-            const int e = k * 32 + lane;
-            v[k] = e < len ? edges[a + e] : INT32_MAX;
-        }
-        warp_bitonic_sort<SORT_EPL>(v);
-        const uint32_t keep = warp_run_starts<SORT_EPL>(v);
-        int total;
-        int before = warp_exclusive_scan(__popc(keep), &total);
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < SORT_EPL; ++k)
-            if (keep & (1u << k)) edges[a + before++] = v[k];
-        if (lane == 0) count[i] = total;
-    }
-}
-
 // Row i: mark the (duplicated) edge list, then count or write it sorted.  The
 // bitmap covers only the row's window [min, max] of neighbour indices (32-bit
-// aligned), so the clear and the compaction cost the window, not n.  With
-// min_len > 0, rows of at most min_len edges are skipped (k_row_unique_warp
-// takes them).
+// aligned), so the clear and the compaction cost the window, not n.
 __global__ void k_row_unique(int32_t n, const int64_t* off, const int32_t* edges,
-                             int64_t* count, const int64_t* out_ptr, int32_t* out_idx, int64_t min_len) {
+                             int64_t* count, const int64_t* out_ptr, int32_t* out_idx) {
     extern __shared__ uint32_t words[];
     __shared__ int64_t scan[ROW_THREADS];
     __shared__ int32_t red[2 * (ROW_THREADS / 32)];
     for (int32_t i = blockIdx.x; i < n; i += gridDim.x) {
-        if (off[i + 1] - off[i] <= min_len) continue;
         int32_t jmin = INT32_MAX, jmax = -1;
         for (int64_t e = off[i] + threadIdx.x; e < off[i + 1]; e += blockDim.x) {
             const int32_t j = edges[e];
@@ -276,9 +238,8 @@ extern "C" int gb_graph_build(gb_handle* h, const gb_csr* H, const gb_csc* D_pre
     // unique neighbour counts of the symmetrised graph; each row's sorted
     // unique list is written in place over the front of its edge list
     GB_CUDA(cudaMemsetAsync(L.ucnt + n, 0, sizeof(int64_t), s));
-    GB_LAUNCH(h, k_row_unique_warp, row_grid(n), ROW_THREADS, 0, n, (const int64_t*)L.cnt, L.edges, L.ucnt);
     GB_LAUNCH(h, k_row_unique, rg, ROW_THREADS, smem, n, (const int64_t*)L.cnt,
-              (const int32_t*)L.edges, L.ucnt, (const int64_t*)L.cnt, L.edges, (int64_t)SORT_MAX);
+              (const int32_t*)L.edges, L.ucnt, (const int64_t*)L.cnt, L.edges);
     GB_TRY(exclusive_scan_i64(h, L.ucnt, L.ucnt, n + 1, L.scan_tmp));
 
     int herr = 0;
