@@ -62,6 +62,18 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int32_t 
 // input checks and Gershgorin bounds of every principal submatrix
 // ---------------------------------------------------------------------------
 // (on the exponent bits: no FP64 instruction per element)
+// h1_offdiag[0] |= 1 if row i of a perturbation holds an entry off the diagonal
+__global__ void k_h1_offdiag(int32_t n, const int64_t* ptr, const int32_t* idx, int* flag) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int64_t p = ptr[i]; p < ptr[i + 1]; ++p) {
+        if (idx[p] != i) {
+            atomicOr(flag, 1);
+            return;
+        }
+    }
+}
+
 __global__ void k_check_finite(int64_t nnz, const double* v, int* err) {
     const unsigned long long* u = (const unsigned long long*)v;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
@@ -536,6 +548,8 @@ struct DensityLayout {
     float* hblk;        // split: (1 + m) * pool_stride dense gathered blocks (FP32)
     double* hdiag;      // split: sub_nnz FP64 diagonals of h^(i)
     double* h1max;      // split: n_sub * m largest |h1| row sums
+    float* h1d;         // split, m > 0: m * sub_nnz diagonals of beta h1 (diagonal H1)
+    int* h1flag;        // split: set when some H1_r has an off-diagonal entry
     int32_t* work;      // split: subgraph lists of the three size classes (3 x n_sub)
     int32_t* work_n;    // split: their lengths (3) and the tiled launch's work counter
     uint8_t* big;       // split, |S_i| > 128: per-CTA scratch of the tiled kernel
@@ -602,6 +616,8 @@ DensityLayout layout_density(Arena& ar, const gb_part* P, int32_t m, int precisi
         L.hblk = nullptr;
         L.hdiag = nullptr;
         L.h1max = nullptr;
+        L.h1d = nullptr;
+        L.h1flag = nullptr;
         L.big = nullptr;
     } else if (precision == GB_PREC_FP64) {
         // sum_i n_i^2 <= max_sub * sum_i n_i
@@ -613,6 +629,8 @@ DensityLayout layout_density(Arena& ar, const gb_part* P, int32_t m, int precisi
         L.hblk = nullptr;
         L.hdiag = nullptr;
         L.h1max = nullptr;
+        L.h1d = nullptr;
+        L.h1flag = nullptr;
     } else {
         // sum_i round16(n_i)^2 <= (max_sub + 15) * (sum_i n_i + 15 n_sub)
         // (a multiple of 64 elements: every block stays 16-byte aligned for the
@@ -624,6 +642,8 @@ DensityLayout layout_density(Arena& ar, const gb_part* P, int32_t m, int precisi
         L.hblk = ar.take<float>((1 + m) * L.pool_stride);
         L.hdiag = ar.take<double>(P->sub_nnz);
         L.h1max = ar.take<double>(n_sub * (int64_t)(m > 0 ? m : 1));
+        L.h1d = ar.take<float>((int64_t)(m > 0 ? m : 1) * P->sub_nnz);
+        L.h1flag = ar.take<int>(4);
         L.work = ar.take<int32_t>(3 * n_sub);
         L.work_n = ar.take<int32_t>(8);
         L.big = nullptr;
@@ -835,6 +855,9 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
     a.hblk_stride = L.pool_stride;
     a.hdiag = L.hdiag;
     a.h1max = L.h1max;
+    a.h1d = L.h1d;
+    a.h1d_stride = P->sub_nnz;
+    a.h1_offdiag = L.h1flag;
     a.big_scratch = L.big;
     a.big_stride = L.big_stride;
     a.big_npmax = L.big_npmax;
@@ -855,6 +878,11 @@ extern "C" int gb_density_and_response(gb_handle* h, const gb_csr* H, const gb_c
         if (lists)
             GB_LAUNCH(h, k_class_lists, 1, CLASS_THREADS, 0, n_sub, P->sub_ptr, o.split_small_npad, L.work,
                       L.work_n);
+        // diagonal perturbations (the water workloads' H1 = diag(v)) skip the
+        // dense h1 blocks of the one-tile subgraphs
+        GB_CUDA(cudaMemsetAsync(L.h1flag, 0, sizeof(int), st));
+        for (int r = 0; r < m; ++r)
+            GB_LAUNCH(h, k_h1_offdiag, (n + tb - 1) / tb, tb, 0, n, H1[r].ptr, H1[r].idx, L.h1flag);
         GB_TRY(launch_split_gather(h, a, L.hblk, L.hdiag));
     } else {
         GB_LAUNCH(h, k_gershgorin, sub_grid, GERSH_THREADS, 0, n_sub, P->sub_ptr, P->sub_idx, H->ptr, H->idx,

@@ -101,6 +101,14 @@ struct PassArgs {
     const double* hdiag;
     // split path: largest row sum of |h1_r^(i)|, at h1max[i * m + r]
     double* h1max;
+    // split path, diagonal perturbations (h1_offdiag[0] == 0: every entry of
+    // every H1_r lies on the diagonal, set by k_h1_offdiag before the
+    // gather): the one-tile subgraphs' beta h1_r^(i) is kept as its diagonal
+    // alone, at h1d[r * h1d_stride + sub_ptr[i] + row] (the same FP32 values
+    // the dense block would hold), and no dense h1 block is written for them
+    float* h1d;
+    int64_t h1d_stride;
+    const int* h1_offdiag;
     // tiled split path (|S_i| > 128): per-CTA scratch (big_stride bytes each,
     // laid out for subgraphs of up to big_npmax = round16(max |S_i|) orbitals)
     // and the dynamic work counter of the launch (zeroed before it)

@@ -179,6 +179,7 @@ struct Kernel {
     uint32_t lane_off;
     uint32_t lo_off;          // bytes from a staged operand's hi part to its lo part (npad x 256)
     uint32_t zc, xc, pl, pr;  // TMEM columns: Z, X (FP32 state), product left / right halves
+    bool diag_h1;             // the perturbations are diagonal: X1 staged from a.h1d
 
     __device__ Kernel(const PassArgs& a_, Ctl& c_, uint8_t* smem) : a(a_), c(c_) {
         st0 = smem;
@@ -191,6 +192,7 @@ struct Kernel {
         row = threadIdx.x & 127;
         grp = threadIdx.x >> 7;
         lane_off = (uint32_t)((row & ~31) << 16);
+        diag_h1 = a.m > 0 && a.h1_offdiag && *a.h1_offdiag == 0;
     }
 
     // Per-subgraph layout.  Staged operand: hi part in 8-column groups 2048 B
@@ -708,7 +710,7 @@ struct Kernel {
         const int64_t ni = a.sub_ptr[i + 1] - a.sub_ptr[i];
         const int64_t np = (ni + 15) & ~(int64_t)15;
         const int64_t bytes = np * np * (int64_t)sizeof(float);
-        for (int b = 0; b <= a.m; ++b) {
+        for (int b = 0; b <= (diag_h1 ? 0 : a.m); ++b) {
             const char* base = (const char*)(a.hblk + (int64_t)b * a.hblk_stride + a.boff[i]);
             for (int64_t o = (int64_t)threadIdx.x * 128; o < bytes; o += (int64_t)THREADS * 128)
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(base + o));
@@ -783,6 +785,25 @@ struct Kernel {
                 for (int j = 0; j < 8; ++j)
                     if (c0 + j == row) v[j] = dv;
             }
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) split_pair(v[2 * j], v[2 * j + 1], fmt, hi[j], lo[j]);
+            uint8_t* p = st(sg) + elem_off(row, c0);
+            *(uint4*)p = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *(uint4*)(p + lo_off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+    }
+
+    // staged operand sg <- scale x diag(d) (d[r]: the FP32 diagonal of beta h1
+    // at row r), zero elsewhere: what stage_dense writes for a diagonal block
+    __device__ void stage_diag(const float* d, float scale, int sg) {
+        const float dv = row < n ? d[row] * (scale * STAGE_SCALE) : 0.f;
+        const int nu = npad / 8;
+        for (int u = grp; u < nu; u += GROUPS) {
+            const int c0 = 8 * u;
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = c0 + j == row ? dv : 0.f;
             uint32_t hi[4], lo[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) split_pair(v[2 * j], v[2 * j + 1], fmt, hi[j], lo[j]);
@@ -902,7 +923,9 @@ __global__ void __launch_bounds__(THREADS, GB_SPLIT_MINB) GB_SPLIT_KERNEL(PassAr
             const float* h1b = a.hblk + (int64_t)(1 + r) * a.hblk_stride + a.boff[i];
             const float x1scale = ldexpf(1.f, -(s + 1) - c.sigk[r]);
             // dZ0 = X1 T + x0 T1,  T1 = -Q1/3 + (2/15)(Q Q1 + Q1 Q),  Q1 = x0 X1 + X1 x0
-            K.stage_dense(h1b, x1scale, false, 0.f, 1);                   // S1 = X1
+            const float* h1d = a.h1d + (int64_t)r * a.h1d_stride + s0;
+            if (K.diag_h1) K.stage_diag(h1d, x1scale, 1);                  // S1 = X1
+            else K.stage_dense(h1b, x1scale, false, 0.f, 1);
             if (!(ok = K.gemm2(0, 1, 1, 0))) break;                        // P = Q1
             K.combine(K.Pk(1.f), K.none(), 0.f, -1, 1, nullptr);           // S1 = Q1
             K.combine(K.T(K.xc, 1.f), K.none(), 0.f, -1, 2, nullptr);      // S2 = Q
@@ -910,7 +933,8 @@ __global__ void __launch_bounds__(THREADS, GB_SPLIT_MINB) GB_SPLIT_KERNEL(PassAr
             K.combine(K.S(1, -1.f / 3.f), K.Pk(2.f / 15.f), 0.f, -1, 1, nullptr);  // S1 = T1
             if (!(ok = K.gemm(0, 1))) break;                               // P = x0 T1
             K.combine(K.T(K.zc, 1.f), K.none(), 0.f, -1, 2, nullptr);      // S2 = T
-            K.stage_dense(h1b, x1scale, false, 0.f, 1);                   // S1 = X1
+            if (K.diag_h1) K.stage_diag(h1d, x1scale, 1);                  // S1 = X1
+            else K.stage_dense(h1b, x1scale, false, 0.f, 1);
             if (!(ok = K.gemm(1, 2, true))) break;                         // P += X1 T
             K.combine(K.Pk(1.f), K.none(), 0.f, -1, -1, z1base + (size_t)r * STAGE_BYTES);
         }
@@ -1051,16 +1075,21 @@ __global__ void __launch_bounds__(256) k_gather_dense(PassArgs a, float* hblk, d
     __shared__ float wmax[8], wlo[8], whi[8], wab[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float bf = d2f_rn(a.beta);
+    const bool diag_h1 = a.m > 0 && a.h1_offdiag && *a.h1_offdiag == 0;
     for (int32_t i = blockIdx.x; i < a.n_sub; i += gridDim.x) {
         const int64_t s0 = a.sub_ptr[i];
         const int n = (int)(a.sub_ptr[i + 1] - s0);
         const int npad = (n + 15) & ~15;
+        // diagonal perturbations of a one-tile subgraph: only their diagonal
+        const bool d1 = diag_h1 && n <= NMAX;
         for (int r = threadIdx.x; r < n; r += blockDim.x) {
             S[r] = a.sub_idx[s0 + r];
             hdiag[s0 + r] = 0.0;
+            if (d1)
+                for (int b = 0; b < a.m; ++b) a.h1d[(int64_t)b * a.h1d_stride + s0 + r] = 0.f;
         }
         // blocks start on 64-element boundaries: zero them 16 bytes at a time
-        for (int b = 0; b <= a.m; ++b) {
+        for (int b = 0; b <= (d1 ? 0 : a.m); ++b) {
             float4* blk4 = (float4*)(hblk + (int64_t)b * a.hblk_stride + a.boff[i]);
             for (int e = threadIdx.x; e < npad * npad / 4; e += blockDim.x) blk4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
@@ -1085,7 +1114,8 @@ __global__ void __launch_bounds__(256) k_gather_dense(PassArgs a, float* hblk, d
                     if (lo < n && S[lo] == col) {
                         const double x = val[p];
                         const float xf = d2f_rn(x), v = bf * xf;
-                        blk[((size_t)(lo >> 2) * npad + r) * 4 + (lo & 3)] = v;
+                        if (b > 0 && d1) a.h1d[(int64_t)(b - 1) * a.h1d_stride + s0 + r] = v;  // lo == r
+                        else blk[((size_t)(lo >> 2) * npad + r) * 4 + (lo & 3)] = v;
                         if (b == 0) {
                             if (lo == r) {
                                 hdiag[s0 + r] = x;
