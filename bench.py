@@ -66,6 +66,15 @@ def recorded_traffic():
         return None
 
 
+def extrapolated_mu(hist, g):
+    """Starting mu for trajectory geometry g from the accepted (geometry, mu)
+    pairs so far: linear extrapolation from the two previous geometries when
+    they are g - 2 and g - 1, else the last accepted mu (nan if none)."""
+    if len(hist) >= 2 and hist[-1][0] == g - 1 and hist[-2][0] == g - 2:
+        return 2.0 * hist[-1][1] - hist[-2][1]
+    return hist[-1][1] if hist else math.nan
+
+
 def rank_barrier(world, dist):
     """All ranks meet before a timed step (no-op on one rank)."""
     if world > 1:
@@ -534,14 +543,10 @@ def run_trajectory(args, rank, world):
                 R.D.val.to("cpu", non_blocking=True)] + [d.val.to("cpu", non_blocking=True) for d in R.D1])
         return P, R, out
 
-    # the starting mu of a step: the previous geometry's mu, extrapolated
-    # linearly from the two before it when they are consecutive geometries
     hist = []
 
     def mu_start(g):
-        if len(hist) >= 2 and hist[-1][0] == g - 1 and hist[-2][0] == g - 2:
-            return 2.0 * hist[-1][1] - hist[-2][1]
-        return hist[-1][1] if hist else math.nan
+        return extrapolated_mu(hist, g)
 
     for g in range(max(args.warmup, 3)):
         _, R, _ = step(g, "fp16x3", mu_start(g))

@@ -83,3 +83,13 @@ def test_csc_asymmetry_of_a_collected_matrix():
     t[5, 2], t[2, 5] = 0.75, 0.0   # one side absent
     m2 = sp.csc_matrix(t)
     assert abs(bench.csc_asymmetry(n, m2.indptr, m2.indices, m2.data) - max(0.25, 0.75)) < 1e-15
+
+
+def test_trajectory_mu_start_extrapolates_consecutive_geometries():
+    import math
+    import bench
+    assert math.isnan(bench.extrapolated_mu([], 0))
+    assert bench.extrapolated_mu([(0, -7.5)], 1) == -7.5
+    assert bench.extrapolated_mu([(0, -7.5), (1, -7.4)], 2) == 2.0 * -7.4 - -7.5
+    # a jump in the geometry sequence (the timed steps restart at geometry 0)
+    assert bench.extrapolated_mu([(1, -7.4), (2, -7.3)], 0) == -7.3
