@@ -499,3 +499,37 @@ def test_split_tiled_class_beside_one_tile(gb):
     print(f"tiled beside one-tile: {(npads > 128).sum()} tiled of {len(npads)}; max|dD|={eD:.2e} "
           f"max|dD1|={eD1:.2e} dmu={R.mu - ref.mu:.2e}")
     assert eD <= TOL["fp16x3"] and eD1 <= TOL["fp16x3"]
+
+
+@pytest.mark.parametrize("kind", ["diagonal_with_empty_rows", "one_off_diagonal_pair"])
+def test_perturbation_structure(gb, kind):
+    # The split path stages a diagonal perturbation from its diagonal alone and
+    # any other from dense blocks (the choice is made on the device): a
+    # diagonal H1 with some rows left empty, and the same H1 with one
+    # symmetric off-diagonal pair added (which must take the dense path), both
+    # against the oracle.
+    wl, system, h1 = make_workload("water64", n_rhs=1)
+    H = system.H
+    n = H.n
+    v = h1[0].to_dense().diagonal().copy()
+    rows = np.arange(n)[np.arange(n) % 7 != 3]  # every seventh row empty
+    vals = v[rows]
+    if kind == "one_off_diagonal_pair":
+        j, k = int(H.indices[H.indptr[5]]), 5  # an edge of the graph
+        j = j if j != k else int(H.indices[H.indptr[5] + 1])
+        rows = np.concatenate([rows, [j, k]])
+        cols = np.concatenate([np.arange(n)[np.arange(n) % 7 != 3], [k, j]])
+        vals = np.concatenate([vals, [0.03, 0.03]])
+    else:
+        cols = rows
+    P1 = CSR.from_coo(n, rows, cols, vals)
+    adj = o_graph(n, H.indptr, H.indices, H.data, wl.tau)
+    part = o_part(adj, system.orb_group)
+    ref = oracle_graph(H, [P1], wl.kT, system.n_occ, part)
+    Hd = to_device(H)
+    P = gb.partition(gb.graph_build(Hd, wl.tau), torch.as_tensor(system.orb_group))
+    R = gb.density_and_response(Hd, [to_device(P1)], wl.kT, system.n_electrons, P, precision="fp16x3",
+                                mu0=ref.mu)
+    eD, eD1 = max_abs_block_error(R, ref, part)
+    print(f"H1 {kind}: max|dD|={eD:.2e} max|dD1|={eD1:.2e}")
+    assert eD <= TOL["fp16x3"] and eD1 <= TOL["fp16x3"]
