@@ -259,19 +259,28 @@ struct Kernel {
         return make_desc_b(sa_of(sb) + part + (uint32_t)ks * 2u * SBO); // B: 16 rows of K
     }
 
-    // P = A B (acc = false) or P += A B, split in FP16 parts, per K step:
+    // P = A B (acc = false) or P += A B, split in FP16 parts.  Even K steps:
     //   [left | right] += A_hi [B_hi | B_lo]   (one N = 2 npad instruction)
     //   right          += A_lo B_hi
-    // 2 K instructions instead of 3 K: an M = 128 instruction costs the same
-    // for any N <= 256.  The left accumulator holds only the large A_hi B_hi
-    // terms, the right one the small cross terms; the product is left + right.
+    // odd K steps, the large term into the other half:
+    //   right += A_hi B_hi;  left += A_hi B_lo;  left += A_lo B_hi
+    // so each half accumulates the large A_hi B_hi terms of half of the K
+    // steps: the tensor cores' FP32 accumulation rounds toward zero, and two
+    // accumulators at half the magnitude halve that bias (and its spread).
+    // The product is left + right, added by the staging pass.
     __device__ void issue_prod(int sa, int sb, bool acc) {
         const int K = npad / 16;
         const uint32_t id1 = make_idesc(fmt, 0, npad), id2 = make_idesc(fmt, 0, 2 * npad);
         const uint32_t dl = col(pl), dr = col(pr);
         for (int ks = 0; ks < K; ++ks) {
-            mma_f16(dl, da(sa, 0, ks), db(sb, 0, ks), id2, (acc || ks > 0) ? 1u : 0u);
-            mma_f16(dr, da(sa, lo_off, ks), db(sb, 0, ks), id1, 1u);
+            if ((ks & 1) == 0) {
+                mma_f16(dl, da(sa, 0, ks), db(sb, 0, ks), id2, (acc || ks > 0) ? 1u : 0u);
+                mma_f16(dr, da(sa, lo_off, ks), db(sb, 0, ks), id1, 1u);
+            } else {
+                mma_f16(dr, da(sa, 0, ks), db(sb, 0, ks), id1, 1u);
+                mma_f16(dl, da(sa, 0, ks), db(sb, lo_off, ks), id1, 1u);
+                mma_f16(dl, da(sa, lo_off, ks), db(sb, 0, ks), id1, 1u);
+            }
         }
     }
 
