@@ -81,10 +81,10 @@ def test_water1k_parity(gb, precision, kT):
           f"dmu1={R.mu1[0] - ref.mu1[0]:.2e} passes={R.report['passes']} steps={R.report['max_steps']}")
     assert eD <= TOL[precision]
     # With mu solved from split-precision traces, the trace round-off (~1e-7 per
-    # core orbital, random) moves mu by ~2e-5 eV on this 6,000-orbital box at
+    # core orbital, random) moves mu by ~1e-5 eV on this 6,000-orbital box at
     # kT = 0.05, and D1 (which depends on mu through the second derivative of
-    # the Fermi function) by ~1e-5: the closest case to the bound (at the
-    # oracle's mu the split D1 is within 2e-7, test_split_parity_at_fixed_mu).
+    # the Fermi function) by ~7e-6: the closest case to the bound (at the
+    # oracle's mu the split D1 is within 1e-7, test_split_parity_at_fixed_mu).
     assert eD1 <= TOL[precision]
     if ref.trace_core_dd / kT > 1e-6 * system.n_occ:  # mu resolvable above trace precision
         assert abs(R.mu - ref.mu) < (1e-8 if precision == "fp64" else 1e-4)
