@@ -60,6 +60,26 @@ def test_graph_build_matches_pair_enumeration(paths2):
         assert all(np.all(np.diff(adj.neighbours(i)) > 0) for i in range(60))
 
 
+def test_graph_symmetrises_one_sided_entries():
+    # A column-collected D_prev is not symmetric, and an H given as one
+    # triangle is not either: an entry above tau on one side alone makes the
+    # edge both ways (the graph is undirected).
+    rng = np.random.default_rng(23)
+    n, tau = 40, 0.1
+    A = np.triu(_random_sparse_sym(rng, n, 0.05))
+    dprev = rng.normal(size=(n, n)) * (rng.random((n, n)) < 0.04)
+    one_sided = (np.abs(dprev) > tau) & ~(np.abs(dprev.T) > tau)
+    np.fill_diagonal(one_sided, False)
+    assert one_sided.any()
+    Ac, Dc = CSR.from_dense(A), CSR.from_dense(dprev)
+    for paths2 in (False, True):
+        adj = graph_build(n, Ac.indptr, Ac.indices, Ac.data, tau, paths2=paths2,
+                          d_prev=(Dc.indptr, Dc.indices, Dc.data))
+        E = _brute_graph(A, tau, dprev, paths2)
+        assert np.array_equal(E, E.T)
+        assert np.array_equal(adj.to_dense(), E)
+
+
 def test_graph_threshold_is_strict():
     A = np.array([[0.0, 0.5, 0.0], [0.5, 0.0, 0.25], [0.0, 0.25, 0.0]])
     Ac = CSR.from_dense(A + np.eye(3))

@@ -19,8 +19,8 @@ from synth import softened_coulomb_matrix, water_box
 KT = 0.3
 
 
-@pytest.fixture(scope="module")
-def model():
+def krylov_model():
+    """8 waters with the softened Coulomb charge model and off-neutral populations."""
     system = water_box(8, 77)
     C = softened_coulomb_matrix(system.positions, system.box)
     z = system.z_valence
@@ -28,6 +28,11 @@ def model():
     dq = rng.normal(0.0, 0.05, size=system.n_atoms)
     n = z + dq - dq.mean()
     return system, C, z, n
+
+
+@pytest.fixture(scope="module")
+def model():
+    return krylov_model()
 
 
 def residual(system, C, z, part, n):
