@@ -477,6 +477,57 @@ def test_split_water4k_six_rhs(gb):
     assert eD <= TOL["fp16x3"] and eD1 <= TOL["fp16x3"]
 
 
+def test_split_headline_box_full_size(gb):
+    # The 10,000-water box at its full size (60,000 orbitals, kT 0.2 eV,
+    # tau 1e-4) in the launch configuration of the timed step: a cold first
+    # pass on the H graph gives D_1; the graph |H| > tau or |D_1| > tau and the
+    # one-molecule partition are built on the GPU and must equal the oracle's,
+    # built from the same D_1 values, bit for bit; the size classes come from
+    # gb_plan_autotune; the split pass, warm-started from the first pass's mu,
+    # matches the oracle on that graph in every collected element of D and D1
+    # (within 1e-5), in mu, and in the Mulliken charges and their response.
+    import os
+    from oracle.solve import mulliken_charges
+    wl, system, h1 = make_workload("water10k", n_rhs=1)
+    H = system.H
+    Hd, H1d = to_device(H), [to_device(h1[0])]
+    groups = torch.as_tensor(system.orb_group)
+    P0 = gb.partition(gb.graph_build(Hd, wl.tau), groups)
+    R1 = gb.density_and_response(Hd, H1d, wl.kT, system.n_electrons, P0, precision="fp16x3")
+    G = gb.graph_build(Hd, wl.tau, d_prev=R1.D)
+    P = gb.partition(G, groups)
+    d_1 = (R1.D.ptr.cpu().numpy(), R1.D.idx.cpu().numpy(), R1.D.val.cpu().numpy())
+    adj = o_graph(H.n, H.indptr, H.indices, H.data, wl.tau, d_prev=d_1)
+    assert np.array_equal(G.ptr.cpu().numpy(), adj.indptr) and np.array_equal(G.idx.cpu().numpy(), adj.indices)
+    part = o_part(adj, system.orb_group)
+    assert np.array_equal(P.sub_ptr.cpu().numpy(), part.sub_ptr)
+    assert np.array_equal(P.sub_idx.cpu().numpy(), part.sub_idx)
+    plan = gb.plan_autotune(Hd, H1d, wl.kT, system.n_electrons, P, R1.mu)
+    R = gb.density_and_response(Hd, H1d, wl.kT, system.n_electrons, P, precision="fp16x3", mu0=R1.mu,
+                                split_small_npad=plan["split_small_npad"])
+    ref = oracle_graph(H, h1, wl.kT, system.n_occ, part, workers=min(16, os.cpu_count() or 1))
+    assert np.array_equal(R.D.ptr.cpu().numpy(), ref.D[0]) and np.array_equal(R.D.idx.cpu().numpy(), ref.D[1])
+    dval, d1val = R.D.val.cpu().numpy(), R.D1[0].val.cpu().numpy()
+    eD = float(np.abs(dval - ref.D[2]).max())
+    eD1 = float(np.abs(d1val - ref.D1[0][2]).max())
+    # charges from the collected diagonals (column j holds its own row j)
+    aptr, aorb = (torch.as_tensor(np.concatenate([[0], np.cumsum(np.bincount(system.orb_atom))])),
+                  torch.as_tensor(np.argsort(system.orb_atom, kind="stable").astype(np.int32)))
+    q, q1 = gb.mulliken_charges(R.D, R.D1, aptr, aorb, torch.as_tensor(system.z_valence))
+    col = np.repeat(np.arange(H.n), np.diff(ref.D[0]))
+    on_diag = ref.D[1] == col
+    qref = mulliken_charges(ref.D[2][on_diag], system.orb_atom, system.z_valence)
+    q1ref = mulliken_charges(ref.D1[0][2][on_diag], system.orb_atom, np.zeros_like(system.z_valence))
+    eq, eq1 = float(np.abs(q.cpu().numpy() - qref).max()), float(np.abs(q1[0].cpu().numpy() - q1ref).max())
+    print(f"water10k two-pass: sizes {part.sizes().min()}..{part.sizes().max()} plan {plan['split_small_npad']} "
+          f"max|dD|={eD:.2e} max|dD1|={eD1:.2e} dmu={R.mu - ref.mu:.2e} dmu1={R.mu1[0] - ref.mu1[0]:.2e} "
+          f"max|dq|={eq:.2e} max|dq1|={eq1:.2e} passes={R.report['passes']}")
+    assert eD <= TOL["fp16x3"] and eD1 <= TOL["fp16x3"]
+    assert abs(R.mu - ref.mu) <= 1e-4
+    per_atom = int(np.bincount(system.orb_atom).max())
+    assert eq <= 2 * per_atom * TOL["fp16x3"] and eq1 <= 2 * per_atom * TOL["fp16x3"]
+
+
 def test_split_tiled_class_beside_one_tile(gb):
     # a few large subgraphs among many small ones: the tiled kernel runs on
     # its own stream beside the 128-column kernel, and a second launch of the
