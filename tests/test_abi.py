@@ -72,6 +72,36 @@ def test_density_workspace_query(lib):
     assert lib.gb_density_workspace_size(ctypes.byref(p), 99, ctypes.byref(o), ctypes.byref(nb)) == 1
 
 
+def test_density_workspace_follows_the_layout(lib):
+    # host-side size queries against the layout of the workspace: (7 + m)
+    # dense FP64 blocks per subgraph on the FP64 path; on the split path a
+    # tiled-class scratch (16 + 2m staged images of 128 nrb x npmax FP16 hi
+    # and lo parts per CTA) only when a subgraph exceeds 128 orbitals; one
+    # response image per RHS and CTA; argument errors before any sizing
+    from paper_2212_01997_gb300 import _lib
+
+    def size(max_sub, m, precision, n_sub=100, n=600):
+        sub_nnz = n_sub * max_sub
+        p = _lib.gb_part(n, n_sub, max_sub, 6, sub_nnz, sub_nnz * 6, sub_nnz, None, None, None, None, None)
+        o = _lib.gb_opts(precision, 0, 0.0, 0, 0, 0.0)
+        nb = ctypes.c_size_t()
+        st = lib.gb_density_workspace_size(ctypes.byref(p), m, ctypes.byref(o), ctypes.byref(nb))
+        return st, nb.value
+
+    for m in (0, 1, 6):
+        st, fp64 = size(100, m, 0)
+        assert st == 0 and fp64 >= (7 + m) * 100 * (100 * 100) * 8
+    st, small = size(128, 1, 1)
+    st2, big = size(200, 1, 1)
+    assert st == 0 and st2 == 0
+    npmax, nrb = 208, 2
+    assert big - small >= 100 * (16 + 2) * (2 * 128 * nrb * npmax * 2)
+    assert size(128, 2, 1)[1] > size(128, 1, 1)[1] > size(128, 0, 1)[1]
+    assert size(100, 1, 3)[1] >= 100 * (100 * 100) * 8          # eigenvectors of every subgraph
+    assert size(100, 9, 1)[0] == 1 and size(100, -1, 0)[0] == 1  # m beyond 8 RHS, negative m
+    assert size(100, 1, 0, n_sub=0)[0] == 1
+
+
 def test_product_path_has_no_oracle_dependency():
     pkg = os.path.join(ROOT, "paper_2212_01997_gb300")
     for dirpath, _, files in os.walk(pkg):
