@@ -89,6 +89,13 @@ def test_subgraph_blocks_are_charge_neutral_and_inverted(model):
         assert np.abs(k0 @ (jc - alpha * np.eye(3)) - np.eye(3)).max() < 1e-12
         # off the diagonal the response is the susceptibility (it does not vanish)
         assert np.abs(jc + np.eye(3)).max() > 1e-3
+    # K0 is the block diagonal of the k0 blocks over their core atoms (Eq.
+    # PreCond), applied as a matrix: against the assembled dense K0
+    K0 = np.zeros((system.n_atoms, system.n_atoms))
+    for atoms, _, k0 in blocks:
+        K0[np.ix_(atoms, atoms)] = k0
+    x = np.random.default_rng(4).normal(size=system.n_atoms)
+    assert np.abs(apply_preconditioner(blocks, x) - K0 @ x).max() < 1e-12
 
 
 def test_krylov_directional_derivatives(model):

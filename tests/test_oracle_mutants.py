@@ -131,6 +131,10 @@ MUTANTS = [
     ("collect-core-slots-reversed", G, "collect_columns",
      [("slot[c] = np.arange(len(c))", "slot[c] = np.arange(len(c))[::-1]")],
      ["graph:test_sub_f_multi_vertex_cores_column_collect"]),
+    ("gather-columns-reversed", G, "gather",
+     [("return X[s][:, s].toarray()", "return X[s][:, s[::-1]].toarray()"),
+      ("np.asarray(X)[np.ix_(s, s)]", "np.asarray(X)[np.ix_(s, s[::-1])]")],
+     ["graph:test_sub_f_single_vertex_cores", "solve:test_graph_with_one_subgraph_is_full"]),
     ("cap-not-strict", G, "partition_capped",
      [("np.nonzero(sizes > max_sub)", "np.nonzero(sizes >= max_sub)")],
      ["graph:test_partition_capped_rule_by_brute_force"]),
@@ -151,6 +155,9 @@ MUTANTS = [
       "krylov:test_subgraph_blocks_are_charge_neutral_and_inverted"]),
     ("k0-alpha-sign", K, "core_jacobians",
      [("np.linalg.inv(jc - alpha * np.eye(na))", "np.linalg.inv(jc + alpha * np.eye(na))")],
+     ["krylov:test_subgraph_blocks_are_charge_neutral_and_inverted"]),
+    ("preconditioner-block-transposed", K, "apply_preconditioner",
+     [("y[atoms] = k0 @ np.asarray(x)[atoms]", "y[atoms] = k0.T @ np.asarray(x)[atoms]")],
      ["krylov:test_subgraph_blocks_are_charge_neutral_and_inverted"]),
     ("krylov-drops-minus-v", K, "krylov_update",
      [("apply_preconditioner(blocks, drho - v)", "apply_preconditioner(blocks, drho)")],
