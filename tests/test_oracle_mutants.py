@@ -100,6 +100,9 @@ MUTANTS = [
     ("d1mu-trace-wrong-rows", S, "_response_task",
      [("tr_mu = float(np.trace(d1mu_c[core_local, :]))", "tr_mu = float(np.trace(d1mu_c))")],
      ["solve:test_graph_invariants_and_canonical_finite_difference"]),
+    ("graph-occupation-derivative-uses-f", S, "oracle_graph",
+     [("tr_dd = sum(float(np.dot(fermi_weight(e, mu, kT), w))", "tr_dd = sum(float(np.dot(fermi(e, mu, kT), w))")],
+     ["solve:test_graph_invariants_and_canonical_finite_difference"]),
     ("graph-mu1-term-sign", S, "oracle_graph",
      [("d1_c[r] + mu1[r] * d1mu_c", "d1_c[r] - mu1[r] * d1mu_c")],
      ["solve:test_graph_invariants_and_canonical_finite_difference", "solve:test_graph_exact_on_disconnected_blocks"]),

@@ -126,6 +126,9 @@ def test_graph_invariants_and_canonical_finite_difference(water64):
     assert abs(np.trace(D) - system.n_occ) < 1e-9
     assert abs(np.trace(D1)) < 1e-12
     assert abs(g.trace_core - system.n_occ) < 1e-9
+    # dN/dmu two ways: beta sum_k f(1 - f) w_k from the spectra, and the core
+    # traces of the d1_mu = beta d (I - d) matrices (Eq. dddmu)
+    assert abs(g.trace_d1mu - g.trace_core_dd / wl.kT) < 1e-10 * g.trace_d1mu
     # canonical finite difference on the same graph, mu re-solved each side
     e = 1e-4
     Hp = CSR(H.n, H.indptr, H.indices, H.data.copy())
