@@ -118,3 +118,22 @@ def test_perturbation_recipe(water64):
     dq = np.linalg.solve(Cd, v)
     assert abs(dq.sum()) < 1e-8
     assert 0.07 < dq.std() < 0.13
+
+
+def test_thermal_trajectory_recipe(water64):
+    # force-free steps x += v dt (dt 0.25 fs, wrapped) with Maxwell velocities
+    # at 300 K: constant displacement per step, per-axis velocity spread
+    # sqrt(kB T / m) for each species
+    from synth.water import thermal_trajectory
+    s = water64
+    steps = list(thermal_trajectory(s, 3, seed=20221204 + 1000))
+    d1 = _min_image(steps[0] - s.positions, s.box)
+    d2 = _min_image(steps[1] - steps[0], s.box)
+    np.testing.assert_allclose(d2, d1, atol=1e-12)
+    assert np.all((steps[2] >= 0) & (steps[2] < s.box))
+    v = d1 / 0.25                                              # A/fs
+    kB, conv = 8.617333262e-5, 0.0982269                       # eV/K; sqrt(eV/amu) in A/fs
+    for code, mass in ((0, 1.008), (3, 15.999)):
+        sigma = np.sqrt(kB * 300.0 / mass) * conv
+        got = v[s.species == code].std()
+        assert abs(got / sigma - 1.0) < 0.15, (code, got, sigma)
