@@ -93,3 +93,18 @@ def test_trajectory_mu_start_extrapolates_consecutive_geometries():
     assert bench.extrapolated_mu([(0, -7.5), (1, -7.4)], 2) == 2.0 * -7.4 - -7.5
     # a jump in the geometry sequence (the timed steps restart at geometry 0)
     assert bench.extrapolated_mu([(1, -7.4), (2, -7.3)], 0) == -7.3
+
+
+def test_recorded_traffic_only_for_the_sources_it_was_taken_on(tmp_path, monkeypatch):
+    # the roofline's DRAM traffic comes from a recorded ncu capture only while
+    # the recursion kernel's sources still hash to what the record names
+    import json
+    rec = {"kernel": "k_fermi_split", "traffic_bytes_per_launch": 123456789}
+    path = tmp_path / "traffic.json"
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(path))
+    path.write_text(json.dumps(dict(rec, kernel_source_sha256=bench.kernel_source_hash())))
+    assert bench.recorded_traffic() == 123456789.0
+    path.write_text(json.dumps(dict(rec, kernel_source_sha256="0" * 64)))
+    assert bench.recorded_traffic() is None
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "missing.json"))
+    assert bench.recorded_traffic() is None
