@@ -63,3 +63,20 @@ def test_entry_point_arities_match_the_header():
     assert len(protos) == len(_lib.SIGNATURES)
     for name, _, args in _lib.SIGNATURES:
         assert protos[name] == len(args), name
+
+
+def test_status_and_precision_codes_match_the_header(tmp_path):
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    names = list(_lib.STATUS.values()) + ["GB_PREC_FP64", "GB_PREC_FP16X3", "GB_PREC_BF16X3", "GB_PREC_EIGEN"]
+    src = tmp_path / "codes.c"
+    src.write_text("\n".join(['#include <stdio.h>', '#include "gbqr.h"', "int main(void) {"] +
+                             [f'printf("{n} %d\\n", (int){n});' for n in names] + ["return 0;", "}"]))
+    exe = tmp_path / "codes"
+    subprocess.run([cc, "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {line.split()[0]: int(line.split()[1]) for line in out if line}
+    assert {v: k for k, v in _lib.STATUS.items()} == {n: got[n] for n in _lib.STATUS.values()}
+    prec = {"fp64": "GB_PREC_FP64", "fp16x3": "GB_PREC_FP16X3", "bf16x3": "GB_PREC_BF16X3", "eigen": "GB_PREC_EIGEN"}
+    assert {k: got[v] for k, v in prec.items()} == _lib.PRECISION
