@@ -106,6 +106,9 @@ MUTANTS = [
     ("graph-mu1-term-sign", S, "oracle_graph",
      [("d1_c[r] + mu1[r] * d1mu_c", "d1_c[r] - mu1[r] * d1mu_c")],
      ["solve:test_graph_invariants_and_canonical_finite_difference", "solve:test_graph_exact_on_disconnected_blocks"]),
+    ("graph-mu1-sign", S, "oracle_graph",
+     [("mu1 = -tr1 / tr_mu if m else np.zeros(0)", "mu1 = tr1 / tr_mu if m else np.zeros(0)")],
+     ["solve:test_graph_exact_on_disconnected_blocks"]),
     ("mulliken-sign", S, "mulliken_charges",
      [("return z_val - pop", "return pop - z_val")],
      ["solve:test_mulliken_two_atom_closed_form"]),

@@ -112,6 +112,7 @@ def test_graph_exact_on_disconnected_blocks():
     np.testing.assert_allclose(csc_to_dense(n, *g.D), full.D, atol=1e-12)
     np.testing.assert_allclose(csc_to_dense(n, *g.D1[0]), full.D1[0], atol=1e-10)
     assert abs(g.mu - full.mu) < 1e-10
+    assert abs(g.mu1[0] - full.mu1[0]) < 1e-9 * max(1.0, abs(full.mu1[0]))   # Eq. dmu_1 from core traces
 
 
 def test_graph_invariants_and_canonical_finite_difference(water64):
