@@ -19,7 +19,9 @@ extern "C" int gb_create(gb_handle** h, void* stream) {
     p->aux = nullptr;
     p->ev_fork = p->ev_join = nullptr;
     p->plan_valid = 0;
-    if (cudaGetDevice(&p->device) != cudaSuccess) {
+    const cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        gb_note_device_error(e);
         delete p;
         return GB_ERR_DEVICE;
     }

@@ -1172,9 +1172,11 @@ extern "C" int gb_plan_autotune(gb_handle* h, const gb_csr* H, const gb_csr* H1,
         const int64_t n_sub = P->n_sub;
         int64_t* sp = new (std::nothrow) int64_t[n_sub + 1];
         if (!sp) return GB_ERR_ARG;
-        if (cudaMemcpyAsync(sp, P->sub_ptr, sizeof(int64_t) * (n_sub + 1), cudaMemcpyDeviceToHost, h->stream) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaError_t e = cudaMemcpyAsync(sp, P->sub_ptr, sizeof(int64_t) * (n_sub + 1), cudaMemcpyDeviceToHost,
+                                        h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+            gb_note_device_error(e);
             delete[] sp;
             return GB_ERR_DEVICE;
         }

@@ -453,9 +453,9 @@ int current_context(CUcontext* ctx) {
     if (!f) {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !p)
-            return GB_ERR_DEVICE;
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) gb_note_device_error(e);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) return GB_ERR_DEVICE;
         f = (CtxGetCurrent)p;
         fn.store(f);
     }
@@ -477,7 +477,9 @@ int noalloc_scratch(void** out) {
         // (the lookup also brings up the device's primary context when no
         // runtime call has yet)
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_partition_scratch) != cudaSuccess || !p) return GB_ERR_DEVICE;
+        const cudaError_t ce = cudaGetSymbolAddress(&p, g_partition_scratch);
+        if (ce != cudaSuccess) gb_note_device_error(ce);
+        if (ce != cudaSuccess || !p) return GB_ERR_DEVICE;
         if (!ctx) GB_TRY(current_context(&ctx));
         e.ctx = ctx;
         e.ptr = p;

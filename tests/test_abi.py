@@ -110,3 +110,18 @@ def test_product_path_has_no_oracle_dependency():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "synth" not in src, f
+
+
+def test_device_errors_name_their_cause(lib):
+    # without a usable GPU, gb_create fails with GB_ERR_DEVICE and the CUDA
+    # error behind it is reported (gb_last_device_error), not left at success
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: gb_create succeeds")
+    h = ctypes.c_void_p()
+    assert lib.gb_create(ctypes.byref(h), None) == 7
+    name = ctypes.c_char_p()
+    code = lib.gb_last_device_error(ctypes.byref(name))
+    assert code != 0 and name.value.startswith(b"cuda") and name.value != b"cudaSuccess"
+    from paper_2212_01997_gb300 import _lib
+    assert "CUDA error" in str(_lib.GbError("gb_create", 7))
