@@ -125,3 +125,14 @@ def test_device_errors_name_their_cause(lib):
     assert code != 0 and name.value.startswith(b"cuda") and name.value != b"cudaSuccess"
     from paper_2212_01997_gb300 import _lib
     assert "CUDA error" in str(_lib.GbError("gb_create", 7))
+
+
+def test_noalloc_scratch_holds_the_largest_accepted_partition(lib):
+    # the allocation-free partition runs gb_partition's code in a fixed array:
+    # that array must hold gb_partition's workspace at the largest size it
+    # accepts (65,536 vertices and groups), for any number of edges
+    cap = lib.gb_partition_noalloc_scratch_bytes()
+    for nnz in (0, 10 ** 6, 10 ** 9):
+        for groups in (0, 1, 65536):
+            assert lib.gb_partition_workspace_size(65536, nnz, groups) <= cap
+    assert 2_000_000 < cap < 2_200_000        # "about 2.1 MB", as the header states
