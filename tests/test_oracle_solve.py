@@ -183,3 +183,19 @@ def test_mulliken_response_is_the_charge_derivative():
     qp = mulliken_charges(np.diag(oracle_full(H + eps * H1, [], kT, nocc).D), atom, z)
     qm = mulliken_charges(np.diag(oracle_full(H - eps * H1, [], kT, nocc).D), atom, z)
     assert np.abs((qp - qm) / (2 * eps) - q1).max() < 1e-7
+
+
+def test_graph_oracle_is_the_same_serial_and_in_a_process_pool(water64):
+    # the tests and the CPU baseline run the oracle over a process pool: every
+    # subgraph's block lands in its own place and the sums keep their order.
+    # The pool's workers run single-threaded BLAS, so a product may round
+    # differently in its last bit; nothing more may change.
+    wl, system, h1 = water64
+    H = system.H
+    part = partition(graph_build(H.n, H.indptr, H.indices, H.data, wl.tau), system.orb_group)
+    a = oracle_graph(H, h1, wl.kT, system.n_occ, part, workers=0)
+    b = oracle_graph(H, h1, wl.kT, system.n_occ, part, workers=2)
+    assert abs(a.mu - b.mu) < 1e-13 and np.abs(a.mu1 - b.mu1).max() < 1e-13
+    for x, y in zip([a.D] + a.D1, [b.D] + b.D1):
+        assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+        assert np.abs(x[2] - y[2]).max() < 1e-15
